@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Kron-STAP throughput benchmark on B300.
+
+One step = the whole per-cell hot path (kstap_fit_project + kstap_detect:
+frame scale, exact lag-sum moments, Alg. 2 flip-flop, B / U_B fit, Eq.
+KronSTAP projection and velocity bank) over one synthetic 1024 x 1024-cell
+frame (p = 3, q = 16, r_b = 3, n = 120, V = 64, 40 dB CNR, 200 targets).
+
+value  : test cells/s with the frame resident in HBM (sum of per-step CUDA
+         event times; a 256 MiB L2 flush runs between steps, outside the events)
+e2e    : the same metric through the C ABI with the frame in pinned host memory:
+         H2D copy + fit + detect + D2H of Tmax / vidx / map inside the events
+N > 1  : one rank per GPU, each on its own frame (independent problems, no
+         collective on the data path): weak scaling, value = all cells / max time.
+--impl reference : the FP64 CPU oracle timed on a bounded sample of the same
+         workload's cells (host cores), same metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Kron-STAP test cells/s and p50/p99 frame latency on 1 B300, batched vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kstap", choices=["kstap", "reference"])
+    ap.add_argument("--workload", default="frame1024")
+    ap.add_argument("--cpu-sample", type=int, default=1024,
+                    help="cells of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------- reference arm --
+def run_reference(args):
+    import gen
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = gen.WORKLOADS[args.workload]
+    f = gen.make_frame(wl)
+    nthr = oracle.num_threads()
+    sample = max(64, args.cpu_sample // 4)
+    times = []
+    for s in range(args.warmup + args.steps):
+        cells = gen.random_cells(wl, sample, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.run_workload(f, cells=cells, want_T_all=False, want_proj=False)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample * len(times) / total
+    line = dict(metric=METRIC, value=value, unit="cells/s", n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * total / len(times),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=wl.name, cells_per_frame=wl.H * wl.W, q=wl.q, r_b=wl.r_b,
+                            n=wl.n, V=wl.V, p=wl.p, sample_cells_per_step=sample),
+                cpu_baseline=dict(value=value, unit="cells/s", cores=nthr, kind="oracle",
+                                  sample=f"{sample} seeded random cells per step of the "
+                                         f"{wl.H}x{wl.W} frame"),
+                e2e=dict(value=value, unit="cells/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.index = index
+        self.proc = None
+        self.path = None
+        if enabled:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            try:
+                self.fh = open(self.path, "w")
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                     "-i", str(index), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+
+
+# ------------------------------------------------------------ work model ---
+def work_per_cell(wl):
+    """Algorithmic arithmetic per cell of each kernel.
+
+    Units: single-precision flops (FMA = 2) for floating point, and integer
+    multiply-adds (one 32x32->64 product-accumulate = 2 ops) for the exact
+    lag sums; a float-float product-accumulate counts as 2 flops (the flops
+    of the exact-arithmetic formula, not of its emulation).
+    """
+    p, q, rb, V = wl.p, wl.q, wl.r_b, wl.V
+    PP = p * p
+    NE = PP * (PP + 1) // 2
+    NR = 2 * wl.ring_r + 1
+    tc = 32 if q < 32 else 16
+    # lag sums for one tile of tc cells, all lags g in [0, q): vertical box
+    # (NR products per plane and column) + horizontal ring (2Ra+1 + 2Ga+1 adds)
+    lag = 0
+    for g in range(q):
+        nu = tc + q - 1 - g
+        kw = nu + 2 * wl.ring_a
+        lag += PP * kw * NR * 8 + PP * nu * (2 * wl.ring_a + 1 + 2 * wl.guard_a + 1) * 2
+    lag_per_cell = lag / tc
+    m_flops = sum(q - g for g in range(q)) * NE * 8
+    b_flops = sum(q - g for g in range(q)) * PP * 8
+    eig_flops = 12 * (q * q * rb * 8)            # ~12 subspace products (FP32 + FF)
+    det_flops = V * (p * q + q * rb + p) * 8 + 2 * p * q * rb * 8
+    return dict(frame_scale=6.0, moments=lag_per_cell + m_flops, flipflop=6 * (PP * PP * 8),
+                bfit=lag_per_cell + b_flops + eig_flops, detect=det_flops)
+
+
+# ------------------------------------------------------------------ main ----
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = gen.WORKLOADS[args.workload]
+    frames = [gen.make_frame(wl, seed=wl.seed + 7919 * rank + s) for s in range(2)]
+    Ys = [torch.from_numpy(f.Y).to(dev) for f in frames]
+    stream = torch.cuda.current_stream(dev)
+    ks = KStap.from_workload(wl, frames[0].bank_a, frames[0].bank_b, device=str(dev),
+                             stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ncell = wl.H * wl.W
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for s in range(args.warmup):
+        ks.run(Ys[s % 2])
+    barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    K.kstap_set_profiling(ks.ctx, True)
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    barrier()
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        ev[s][0].record(stream)
+        ks.run(Ys[s % 2])
+        ev[s][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    kt = K.kstap_kernel_times(ks.ctx)
+    K.kstap_set_profiling(ks.ctx, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ncell * args.steps * ws / (total_ms / 1e3)
+
+    # ---- e2e: pinned host frame in, Tmax / vidx / map out, through the C ABI
+    Yh = [torch.from_numpy(f.Y).pin_memory() for f in frames]
+    Yd = torch.empty_like(Ys[0])
+    outh = dict(Tmax=torch.empty(ncell, dtype=torch.float32).pin_memory(),
+                vidx=torch.empty(ncell, dtype=torch.int32).pin_memory(),
+                map=torch.empty(ncell, dtype=torch.uint8).pin_memory())
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(s & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Yd.copy_(Yh[s % 2], non_blocking=True)
+        o = ks.run(Yd)
+        for k in outh:
+            outh[k].copy_(o[k], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = ncell * args.steps * ws / (e2e_total / 1e3)
+    h2d = frames[0].Y.nbytes
+    d2h = ncell * (4 + 4 + 1)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (ALU-bound: see the design doc)
+    work = work_per_cell(wl)
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    achieved = work[dom] * ncell / (per_launch_ms / 1e3) / 1e12
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    peak_clock = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FP32 FMA: 128 lanes/SM
+    peak_max = 148 * 128 * 2 * 2032e6 / 1e12
+    roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak_max, unit="TFLOP/s",
+                frac=achieved / peak_max, frac_at_measured_clock=achieved / peak_clock,
+                traffic=None,
+                peak_note="148 SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock); "
+                          "no measured FP32 peak in MEASURED_PEAKS.json",
+                kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()},
+                kernel_share={k: v[0] / max(sum(x[0] for x in kt.values()), 1e-9)
+                              for k, v in kt.items()})
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        cells = gen.random_cells(wl, args.cpu_sample, seed=99)
+        t0 = time.perf_counter()
+        oracle.run_workload(frames[0], cells=cells, want_T_all=False, want_proj=False)
+        dt = time.perf_counter() - t0
+        cpu = dict(value=len(cells) / dt, unit="cells/s", cores=oracle.num_threads(),
+                   kind="oracle", sample=f"{len(cells)} seeded random cells of the "
+                                         f"{wl.H}x{wl.W} frame (FP64, OpenMP)")
+
+    lat = sorted(step_ms)
+    line = dict(
+        metric=METRIC, value=value, unit="cells/s", n_gpus=ws, steps=args.steps,
+        warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32+ff/i64", data="synthetic",
+        config=dict(workload=wl.name, path="plain", cells_per_frame=ncell, p=wl.p, q=wl.q,
+                    r_a=wl.r_a, r_b=wl.r_b, n=wl.n, V=wl.V, cnr_db=wl.cnr_db,
+                    l2="256 MiB flush between timed steps, outside the events",
+                    parallelism=f"replicas x{ws}"),
+        latency_ms=dict(p50=lat[len(lat) // 2], p99=lat[min(len(lat) - 1,
+                                                            math.ceil(0.99 * len(lat)) - 1)]),
+        e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                 ms_per_step=e2e_total / args.steps),
+        gpu_launches=sum(v[1] for v in kt.values()),
+        roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall)
+    print(json.dumps(line), flush=True)
+    ks.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * kstap.h -- C ABI of libkstap, the B300 (sm_103a) Kronecker STAP hot path.
+ *
+ * Method: Greenewald, Zelnio and Hero, "Kronecker STAP and SAR GMTI".
+ * For every test cell (pixel) of a p-channel SAR frame the library
+ *   1. assembles the p x q space-time snapshot X (x = vec(X^T), Sec. 2) and
+ *      the n training snapshots of the cells in a range x azimuth box around
+ *      it minus a guard box, and forms their sample covariance S (Eq. SCM);
+ *   2. fits S ~ A (x) B with rank(A) <= r_a, rank(B) <= r_b by LR-Kron
+ *      (Alg. 2 on the rearrangement R = R(S) of Alg. 1 / Eq. SVD);
+ *   3. projects X with F_KSTAP = (I - U_A U_A^H) (x) (I - U_B U_B^H)
+ *      (Eq. KronSTAP);
+ *   4. evaluates T_v = |d_v^H P x|^2 / (d_v^H P d_v) over a bank of velocity
+ *      steering vectors d_v = a_v (x) b_v (Eq. Moving, Sec. 6 image
+ *      formation), and reports Tmax = max_v T_v, its argmax and Tmax > tau.
+ *
+ * Frame layout (all calls): Y holds p channel images, each H_in x W_in
+ * complex64 (interleaved re, im), row = range, column = azimuth, channel
+ * planes contiguous: Y[(i * H_in + row) * W_in + col].  The cell grid is
+ * H x W with H = H_in - 2 ring_r and W = W_in - 2 ring_a - q + 1; cell (r, c)
+ * owns X[i][j] = Y_i(r + ring_r, c + ring_a + j), and its training cells are
+ * (r + dr, c + dc) with |dr| <= ring_r, |dc| <= ring_a, excluding
+ * |dr| <= guard_r && |dc| <= guard_a, so n = (2 ring_r + 1)(2 ring_a + 1)
+ * - (2 guard_r + 1)(2 guard_a + 1).  Per-cell outputs are indexed
+ * k = r * W + c.
+ *
+ * Memory: every pointer argument named "device" is a CUDA device pointer
+ * owned by the caller (e.g. a torch tensor's data_ptr()).  The library owns
+ * only its context and the workspace it allocates inside kstap_fit_project
+ * (bounded by the context's HBM budget).  All work is enqueued on the
+ * context's stream; the calls return after enqueueing, without a device
+ * synchronisation, except where stated.
+ *
+ * Errors: every call returns a kstap_status; nothing throws across the ABI.
+ * kstap_last_error(ctx) describes the last failure of that context.
+ */
+#ifndef KSTAP_H_
+#define KSTAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  float re, im;
+} kstap_c64; /* interleaved complex64 */
+
+typedef enum {
+  KSTAP_OK = 0,
+  KSTAP_EINVAL = -1,   /* bad argument; nothing was enqueued */
+  KSTAP_ENOMEM = -2,   /* workspace would exceed the HBM budget, or cudaMalloc failed */
+  KSTAP_ECUDA = -3,    /* a CUDA runtime call failed (see kstap_last_error) */
+  KSTAP_EAGAIN = -4,   /* serving: result not ready / not admitted yet */
+  KSTAP_ETIMEOUT = -5, /* serving: poll timed out */
+  KSTAP_ENOTFOUND = -6 /* serving: unknown ticket */
+} kstap_status;
+
+/* Model and detector parameters.  Notation of the paper: p channels, q
+ * pulses (azimuth window), ranks r_a, r_b of A and B (Eq. SparseOpt), Alg. 2
+ * tolerance eps and iteration cap, detection threshold tau on Tmax.
+ * Limits of this build: p == 3, q in {8, 16, 32}, r_a == 1 (the paper's
+ * rank-one spatial model, Eq. KronCov), 1 <= r_b <= 4 with r_b < q (Sec. 5
+ * warns against r_b close to q), ring >= guard >= 0, n >= 1,
+ * (2 ring_r + 1)(2 ring_a + 1) <= 1024.  Other values give KSTAP_EINVAL. */
+typedef struct {
+  int p, q, r_a, r_b;
+  int ring_r, ring_a, guard_r, guard_a;
+  /* Alg. 2 stopping rule on the GPU: stop when the relative change of the
+   * spatial factor a between iterations is <= eps (eps <= 0 selects 2e-6,
+   * i.e. single-precision stagnation), or after max_iter iterations
+   * (max_iter <= 0 selects 64). */
+  double eps;
+  int max_iter;
+  float tau;
+} kstap_params;
+
+/* Per-cell LR-Kron factors, caller-owned device arrays of H * W cells each.
+ *   UA    : [k][p][r_a]  complex64, orthonormal columns (U_A of Eq. KronSTAP)
+ *   UB_hi : [k][q][r_b]  complex64, U_B rounded to single precision
+ *   UB_lo : [k][q][r_b]  complex64, U_B - UB_hi (float-float low part; the
+ *                        projection of X needs U_B to ~2^-40, Sec. 5)
+ *   lamA  : [k][r_a]     float, eigenvalues of A^ (tr A^ = p normalisation)
+ *   lamB  : [k][r_b]     float, eigenvalues of B^ (same normalisation)
+ *   iters : [k]          int32, Alg. 2 iterations taken
+ *   eta   : [k]          float, |R - a b^T|_F / |R|_F at the final a (Alg. 2)
+ * lamA, lamB, iters and eta may be NULL. */
+typedef struct {
+  kstap_c64* UA;
+  kstap_c64* UB_hi;
+  kstap_c64* UB_lo;
+  float* lamA;
+  float* lamB;
+  int32_t* iters;
+  float* eta;
+} kstap_factors;
+
+typedef struct kstap_ctx kstap_ctx;
+
+/* Create a context.  bank_a (V x p) and bank_b (V x q) are device arrays of
+ * complex64 steering factors a_v, b_v (Eq. Moving: d_v = a_v (x) b_v, up to
+ * normalisation, which T_v does not depend on); the library copies them.
+ * 1 <= V <= 256.  hbm_budget_bytes bounds the workspace (0 = unlimited).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Returns KSTAP_EINVAL for unsupported parameters (see kstap_params). */
+kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
+                          const kstap_c64* bank_b, int V, size_t hbm_budget_bytes,
+                          void* cuda_stream, kstap_ctx** out);
+
+/* Steps 1-2 above (Eq. SCM, Alg. 1 as an index map, Alg. 2, EIG_{r_b} of
+ * B^): fits every cell of the frame Y (device, p x H_in x W_in complex64)
+ * and writes the factors.  Requires H_in >= 2 ring_r + 1 and
+ * W_in >= 2 ring_a + q.  Grows the workspace when needed
+ * (KSTAP_ENOMEM if over budget). */
+kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
+                               const kstap_factors* factors);
+
+/* Steps 3-4 above (Eq. KronSTAP and the velocity bank) with the factors of a
+ * previous kstap_fit_project on the same frame.  Outputs (device, H * W):
+ * Tmax float, vidx int32 (lowest maximising v), map uint8 (Tmax > tau);
+ * T_all (device, [k][V] float) may be NULL.  Velocities whose steering
+ * vector keeps less than 1e-12 of its energy after projection get T_v = 0. */
+kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
+                          const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
+                          float* T_all);
+
+/* Free the context, its workspace and its copies of the bank. */
+kstap_status kstap_destroy(kstap_ctx* ctx);
+
+/* Text of the last error of this context ("" if none).  ctx may be NULL, in
+ * which case the last error of kstap_create on this thread is returned. */
+const char* kstap_last_error(const kstap_ctx* ctx);
+
+/* Kernel identifiers for kstap_kernel_times (launch order within one frame). */
+enum {
+  KSTAP_K_SCALE = 0,    /* frame fixed-point scale (max |component| of Y) */
+  KSTAP_K_MOMENTS = 1,  /* exact lag box sums -> M = R R^H and A_0 (Eq. SCM, Sec. 4 init) */
+  KSTAP_K_FLIPFLOP = 2, /* Alg. 2 iterations on M, EIG_{r_a} (one thread per cell) */
+  KSTAP_K_BFIT = 3,     /* exact lag sums -> B (float-float) -> EIG_{r_b} -> U_B */
+  KSTAP_K_DETECT = 4,   /* Eq. KronSTAP projection and the velocity bank */
+  kstap_nkernels = 5
+};
+
+/* Per-kernel timing for measurement.  When enabled, every launch is
+ * bracketed by CUDA events on the context's stream; kstap_kernel_times
+ * synchronises on the pending events and returns, per kernel id, the summed
+ * milliseconds and launch counts since profiling was (re)enabled.  Enabling
+ * or disabling resets the totals. n = number of entries in the arrays. */
+kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable);
+kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launches, int n);
+
+/* Bytes of workspace kstap_fit_project needs for an H_in x W_in frame with
+ * these parameters (0 on invalid input). */
+size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KSTAP_H_ */

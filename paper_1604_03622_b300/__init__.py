@@ -1,0 +1,136 @@
+"""Python binding of libkstap (include/kstap.h): argument marshalling only.
+
+Every step of the Kron-STAP path runs in the CUDA kernels of libkstap.so; this
+module converts torch tensors / ints to the C ABI's plain pointers and sizes.
+There is no CPU fallback: if the shared library is missing or fails to load,
+importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkstap.so")
+
+KSTAP_OK = 0
+STATUS = {0: "KSTAP_OK", -1: "KSTAP_EINVAL", -2: "KSTAP_ENOMEM", -3: "KSTAP_ECUDA",
+          -4: "KSTAP_EAGAIN", -5: "KSTAP_ETIMEOUT", -6: "KSTAP_ENOTFOUND"}
+
+EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
+            "kstap_last_error", "kstap_workspace_bytes", "kstap_set_profiling",
+            "kstap_kernel_times"]
+KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
+
+
+class KstapParams(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("r_a", ctypes.c_int),
+                ("r_b", ctypes.c_int), ("ring_r", ctypes.c_int), ("ring_a", ctypes.c_int),
+                ("guard_r", ctypes.c_int), ("guard_a", ctypes.c_int), ("eps", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("tau", ctypes.c_float)]
+
+
+class KstapFactors(ctypes.Structure):
+    _fields_ = [("UA", ctypes.c_void_p), ("UB_hi", ctypes.c_void_p), ("UB_lo", ctypes.c_void_p),
+                ("lamA", ctypes.c_void_p), ("lamB", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p)]
+
+
+class KstapError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libkstap.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise KstapError(f"libkstap.so not built ({LIB_PATH}); run "
+                             "python -m paper_1604_03622_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.kstap_create.argtypes = [ctypes.POINTER(KstapParams), P, P, I, Z, P,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+        L.kstap_fit_project.argtypes = [P, P, I, I, ctypes.POINTER(KstapFactors)]
+        L.kstap_detect.argtypes = [P, P, I, I, ctypes.POINTER(KstapFactors), P, P, P, P]
+        L.kstap_destroy.argtypes = [P]
+        L.kstap_last_error.argtypes = [P]
+        L.kstap_last_error.restype = ctypes.c_char_p
+        L.kstap_workspace_bytes.argtypes = [ctypes.POINTER(KstapParams), I, I]
+        L.kstap_workspace_bytes.restype = Z
+        L.kstap_set_profiling.argtypes = [P, I]
+        L.kstap_kernel_times.argtypes = [P, P, P, I]
+        for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
+                     "kstap_set_profiling", "kstap_kernel_times"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _check(st: int, ctx: Optional[int] = None) -> None:
+    if st != KSTAP_OK:
+        msg = lib().kstap_last_error(ctx).decode()
+        raise KstapError(f"{STATUS.get(st, st)}: {msg}")
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def make_params(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, tau, eps=0.0,
+                max_iter=0) -> KstapParams:
+    return KstapParams(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, float(eps),
+                       int(max_iter), float(tau))
+
+
+def kstap_create(params: KstapParams, bank_a, bank_b, V: int, hbm_budget_bytes: int = 0,
+                 stream: int = 0) -> int:
+    """bank_a (V x p), bank_b (V x q): complex64 device tensors.  Returns ctx."""
+    out = ctypes.c_void_p()
+    _check(lib().kstap_create(ctypes.byref(params), _ptr(bank_a), _ptr(bank_b), V,
+                              hbm_budget_bytes, stream or None, ctypes.byref(out)))
+    return out.value
+
+
+def make_factors(UA, UB_hi, UB_lo, lamA=None, lamB=None, iters=None, eta=None) -> KstapFactors:
+    return KstapFactors(_ptr(UA), _ptr(UB_hi), _ptr(UB_lo), _ptr(lamA), _ptr(lamB),
+                        _ptr(iters), _ptr(eta))
+
+
+def kstap_fit_project(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors) -> None:
+    _check(lib().kstap_fit_project(ctx, _ptr(Y), H_in, W_in, ctypes.byref(factors)), ctx)
+
+
+def kstap_detect(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors, Tmax, vidx, map_,
+                 T_all=None) -> None:
+    _check(lib().kstap_detect(ctx, _ptr(Y), H_in, W_in, ctypes.byref(factors), _ptr(Tmax),
+                              _ptr(vidx), _ptr(map_), _ptr(T_all)), ctx)
+
+
+def kstap_destroy(ctx: int) -> None:
+    _check(lib().kstap_destroy(ctx))
+
+
+def kstap_workspace_bytes(params: KstapParams, H_in: int, W_in: int) -> int:
+    return int(lib().kstap_workspace_bytes(ctypes.byref(params), H_in, W_in))
+
+
+def kstap_last_error(ctx: Optional[int]) -> str:
+    return lib().kstap_last_error(ctx).decode()
+
+
+def kstap_set_profiling(ctx: int, enable: bool) -> None:
+    _check(lib().kstap_set_profiling(ctx, 1 if enable else 0), ctx)
+
+
+def kstap_kernel_times(ctx: int):
+    """{kernel name: (total ms, launches)} since profiling was enabled."""
+    n = len(KERNELS)
+    ms = (ctypes.c_float * n)()
+    cnt = (ctypes.c_int32 * n)()
+    _check(lib().kstap_kernel_times(ctx, ms, cnt, n), ctx)
+    return {KERNELS[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}

@@ -1,0 +1,462 @@
+// libkstap: C ABI (include/kstap.h) over the Kron-STAP kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kstap.h"
+#include "kstap_kernels.cuh"
+
+using kstap::Geom;
+
+struct kstap_ctx {
+  kstap_params prm;
+  int V = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  int device = 0;
+  // bank, transposed for the detect kernel: aT [p][V], bT [q][V], norms [2V]
+  float2* bank_aT = nullptr;
+  float2* bank_bT = nullptr;
+  float* bank_n2 = nullptr;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::string err;
+  // optional per-kernel timing: events around every launch on ctx->stream
+  bool profile = false;
+  cudaEvent_t ev[kstap_nkernels + 1][2] = {};
+  float kernel_ms[kstap_nkernels] = {};
+  int kernel_launches[kstap_nkernels] = {};
+  bool ev_pending[kstap_nkernels] = {};
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// Records the start event of kernel `k` (profiling mode only).
+void prof_begin(kstap_ctx* ctx, int k) {
+  if (!ctx->profile) return;
+  if (!ctx->ev[k][0]) {
+    cudaEventCreate(&ctx->ev[k][0]);
+    cudaEventCreate(&ctx->ev[k][1]);
+  }
+  cudaEventRecord(ctx->ev[k][0], ctx->stream);
+}
+
+// Records the end event of kernel `k`; the elapsed time is collected lazily.
+void prof_end(kstap_ctx* ctx, int k) {
+  if (!ctx->profile) return;
+  cudaEventRecord(ctx->ev[k][1], ctx->stream);
+  ctx->ev_pending[k] = true;
+}
+
+// Folds finished launches into the per-kernel totals (synchronises on each
+// pending end event; called before the next launch of the same kernel and by
+// kstap_kernel_times).
+void prof_collect(kstap_ctx* ctx, int k) {
+  if (!ctx->ev_pending[k]) return;
+  cudaEventSynchronize(ctx->ev[k][1]);
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, ctx->ev[k][0], ctx->ev[k][1]) == cudaSuccess) {
+    ctx->kernel_ms[k] += ms;
+    ctx->kernel_launches[k] += 1;
+  }
+  ctx->ev_pending[k] = false;
+}
+
+kstap_status fail(kstap_ctx* ctx, kstap_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_create_err = buf;
+  return st;
+}
+
+#define KSTAP_CUDA(ctx, call)                                                            \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((ctx), KSTAP_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+int ceil_log2(long v) {
+  int k = 0;
+  while ((1L << k) < v) ++k;
+  return k;
+}
+
+bool valid_params(const kstap_params* p, std::string& why) {
+  if (!p) {
+    why = "params is NULL";
+    return false;
+  }
+  if (p->p != 3) {
+    why = "this build supports p == 3";
+    return false;
+  }
+  if (p->q != 8 && p->q != 16 && p->q != 32) {
+    why = "q must be 8, 16 or 32";
+    return false;
+  }
+  if (p->r_a != 1) {
+    why = "r_a must be 1 (rank-one spatial clutter model)";
+    return false;
+  }
+  if (p->r_b < 1 || p->r_b > kstap::kRbMax || p->r_b >= p->q) {
+    why = "r_b must satisfy 1 <= r_b <= 4 and r_b < q";
+    return false;
+  }
+  if (p->ring_r < 0 || p->ring_a < 0 || p->guard_r < 0 || p->guard_a < 0 ||
+      p->guard_r > p->ring_r || p->guard_a > p->ring_a) {
+    why = "need ring >= guard >= 0";
+    return false;
+  }
+  if (p->ring_r > 12 || p->ring_a > 24) {
+    why = "ring_r <= 12 and ring_a <= 24 in this build";
+    return false;
+  }
+  const long nbox = (2L * p->ring_r + 1) * (2L * p->ring_a + 1);
+  const long n = nbox - (2L * p->guard_r + 1) * (2L * p->guard_a + 1);
+  if (n < 1) {
+    why = "training ring is empty (n < 1)";
+    return false;
+  }
+  if (nbox > 1024) {
+    why = "(2 ring_r + 1)(2 ring_a + 1) must be <= 1024";
+    return false;
+  }
+  return true;
+}
+
+Geom make_geom(const kstap_ctx* ctx, int H_in, int W_in) {
+  const kstap_params& p = ctx->prm;
+  Geom g;
+  g.p = p.p;
+  g.q = p.q;
+  g.r_a = p.r_a;
+  g.r_b = p.r_b;
+  g.Rr = p.ring_r;
+  g.Ra = p.ring_a;
+  g.Gr = p.guard_r;
+  g.Ga = p.guard_a;
+  g.H_in = H_in;
+  g.W_in = W_in;
+  g.H = H_in - 2 * p.ring_r;
+  g.W = W_in - 2 * p.ring_a - p.q + 1;
+  const long nbox = (2L * p.ring_r + 1) * (2L * p.ring_a + 1);
+  g.n = (int)(nbox - (2L * p.guard_r + 1) * (2L * p.guard_a + 1));
+  g.V = ctx->V;
+  // |Y| < 2^B per component keeps every box sum of products below 2^62:
+  // 2B + 1 + ceil(log2(nbox)) <= 62.
+  g.B = (61 - ceil_log2(nbox)) / 2;
+  if (g.B > 26) g.B = 26;
+  g.max_iter = p.max_iter > 0 ? p.max_iter : 64;
+  g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
+  g.tau = p.tau;
+  g.tc = (p.q >= 32) ? 16 : kstap::kTileCells;
+  return g;
+}
+
+// workspace layout
+struct WsLayout {
+  size_t flags, Mw, Sw, aw, total;
+};
+
+WsLayout ws_layout(int p, size_t ncell) {
+  const size_t PP = (size_t)p * p, NE = PP * (PP + 1) / 2;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  WsLayout L;
+  L.flags = 0;
+  L.Mw = 256;
+  L.Sw = up(L.Mw + ncell * NE * sizeof(float2));
+  L.aw = up(L.Sw + ncell * PP * sizeof(float2));
+  L.total = up(L.aw + ncell * PP * sizeof(float2));
+  return L;
+}
+
+size_t smem_moments(const Geom& g) {
+  const int P = g.p, PP = P * P, NE = PP * (PP + 1) / 2, TC = kstap::kTileCells;
+  const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + g.q - 1, NUmax = TC + g.q - 1;
+  size_t b = (size_t)P * NR * WT * 8;
+  b += (b & 15);
+  b += 2 * (size_t)PP * WT * 16;
+  b += (size_t)PP * NUmax * 8;
+  b += (size_t)TC * NE * 8 + (size_t)TC * PP * 8;
+  return b;
+}
+
+size_t smem_bfit(const Geom& g) {
+  const int P = g.p, PP = P * P, Q = g.q, TC = g.tc;
+  const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
+  size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
+  b += (size_t)TC * PP * 8;
+  b += (size_t)(kstap::kThreads / 32) * Q * kstap::kRbMax * 8;
+  b += (size_t)PP * NUmax * 16;
+  b += 2 * (size_t)PP * WT * 16;
+  b += (size_t)P * NR * WT * 8;
+  return b;
+}
+
+size_t smem_detect(const Geom& g) {
+  const int P = g.p, Q = g.q, V = g.V;
+  const size_t WS = (size_t)P * Q + 2 * (size_t)Q * kstap::kRbMax + 2 * P;
+  return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + (kstap::kThreads / 32) * WS * 8;
+}
+
+template <int P, int Q>
+kstap_status launch_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, const WsLayout& L,
+                        const kstap_factors* f) {
+  char* ws = (char*)ctx->ws;
+  unsigned* maxbits = (unsigned*)(ws + L.flags);
+  float2* Mw = (float2*)(ws + L.Mw);
+  float2* Sw = (float2*)(ws + L.Sw);
+  float2* aw = (float2*)(ws + L.aw);
+  const size_t ncell = (size_t)g.H * g.W;
+  cudaStream_t s = ctx->stream;
+  KSTAP_CUDA(ctx, cudaMemsetAsync(maxbits, 0, 8, s));
+  const size_t nfloat = 2 * (size_t)g.p * g.H_in * g.W_in;
+  int blocks = (int)std::min<size_t>((nfloat + 1023) / 1024, 148 * 16);
+  if (blocks < 1) blocks = 1;
+  prof_collect(ctx, KSTAP_K_SCALE);
+  prof_begin(ctx, KSTAP_K_SCALE);
+  kstap::k_frame_maxabs<<<blocks, 256, 0, s>>>((const float*)Y, nfloat, maxbits, maxbits + 1);
+  prof_end(ctx, KSTAP_K_SCALE);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+
+  const size_t sm1 = smem_moments(g);
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_moments<P, Q>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells, g.H);
+  prof_collect(ctx, KSTAP_K_MOMENTS);
+  prof_begin(ctx, KSTAP_K_MOMENTS);
+  kstap::k_moments<P, Q><<<grid1, kstap::kThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
+  prof_end(ctx, KSTAP_K_MOMENTS);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+
+  prof_collect(ctx, KSTAP_K_FLIPFLOP);
+  prof_begin(ctx, KSTAP_K_FLIPFLOP);
+  kstap::k_flipflop<P><<<(unsigned)((ncell + 127) / 128), 128, 0, s>>>(
+      Mw, Sw, g, ncell, aw, (float2*)f->UA, f->lamA, f->iters, f->eta);
+  prof_end(ctx, KSTAP_K_FLIPFLOP);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+
+  const size_t sm3 = smem_bfit(g);
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_bfit<P, Q>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+  dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
+  prof_collect(ctx, KSTAP_K_BFIT);
+  prof_begin(ctx, KSTAP_K_BFIT);
+  kstap::k_bfit<P, Q><<<grid3, kstap::kThreads, sm3, s>>>(
+      Y, g, maxbits, aw, (float2*)f->UB_hi, (float2*)f->UB_lo, f->lamB);
+  prof_end(ctx, KSTAP_K_BFIT);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+  return KSTAP_OK;
+}
+
+template <int P, int Q>
+kstap_status launch_detect(kstap_ctx* ctx, const Geom& g, const float2* Y, const kstap_factors* f,
+                           float* Tmax, int32_t* vidx, uint8_t* map, float* T_all) {
+  const size_t ncell = (size_t)g.H * g.W;
+  const size_t sm = smem_detect(g);
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const unsigned grid = (unsigned)((ncell + 7) / 8);
+  prof_collect(ctx, KSTAP_K_DETECT);
+  prof_begin(ctx, KSTAP_K_DETECT);
+  kstap::k_detect<P, Q><<<grid, kstap::kThreads, sm, ctx->stream>>>(
+      Y, g, ctx->bank_aT, ctx->bank_bT, ctx->bank_n2, (const float2*)f->UA,
+      (const float2*)f->UB_hi, (const float2*)f->UB_lo, Tmax, vidx, map, T_all);
+  prof_end(ctx, KSTAP_K_DETECT);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+  return KSTAP_OK;
+}
+
+kstap_status check_frame(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in) {
+  if (!ctx) return KSTAP_EINVAL;
+  if (!Y) return fail(ctx, KSTAP_EINVAL, "Y is NULL");
+  const kstap_params& p = ctx->prm;
+  if (H_in < 2 * p.ring_r + 1 || W_in < 2 * p.ring_a + p.q)
+    return fail(ctx, KSTAP_EINVAL, "frame %dx%d smaller than the training box plus window", H_in,
+                W_in);
+  if ((size_t)p.p * H_in * W_in > ((size_t)1 << 40))
+    return fail(ctx, KSTAP_EINVAL, "frame too large");
+  return KSTAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in) {
+  std::string why;
+  if (!valid_params(params, why)) return 0;
+  const long H = H_in - 2L * params->ring_r;
+  const long W = W_in - 2L * params->ring_a - params->q + 1;
+  if (H < 1 || W < 1) return 0;
+  return ws_layout(params->p, (size_t)H * W).total;
+}
+
+kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
+                          const kstap_c64* bank_b, int V, size_t hbm_budget_bytes,
+                          void* cuda_stream, kstap_ctx** out) {
+  if (!out) return fail(nullptr, KSTAP_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (!valid_params(params, why)) return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
+  if (V < 1 || V > 256) return fail(nullptr, KSTAP_EINVAL, "V must be in [1, 256]");
+  if (!bank_a || !bank_b) return fail(nullptr, KSTAP_EINVAL, "bank is NULL");
+  kstap_ctx* ctx = new kstap_ctx();
+  ctx->prm = *params;
+  ctx->V = V;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->budget = hbm_budget_bytes;
+  cudaGetDevice(&ctx->device);
+  const int p = params->p, q = params->q;
+  std::vector<kstap_c64> ha((size_t)V * p), hb((size_t)V * q);
+  cudaError_t e = cudaMemcpy(ha.data(), bank_a, ha.size() * sizeof(kstap_c64), cudaMemcpyDefault);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hb.data(), bank_b, hb.size() * sizeof(kstap_c64), cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(nullptr, KSTAP_ECUDA, "copying the bank failed: %s", cudaGetErrorString(e));
+  }
+  std::vector<float2> aT((size_t)p * V), bT((size_t)q * V);
+  std::vector<float> n2(2 * (size_t)V);
+  for (int v = 0; v < V; ++v) {
+    double sa = 0, sb = 0;
+    for (int i = 0; i < p; ++i) {
+      const kstap_c64 z = ha[(size_t)v * p + i];
+      aT[(size_t)i * V + v] = make_float2(z.re, z.im);
+      sa += (double)z.re * z.re + (double)z.im * z.im;
+    }
+    for (int j = 0; j < q; ++j) {
+      const kstap_c64 z = hb[(size_t)v * q + j];
+      bT[(size_t)j * V + v] = make_float2(z.re, z.im);
+      sb += (double)z.re * z.re + (double)z.im * z.im;
+    }
+    n2[v] = (float)sa;
+    n2[V + v] = (float)sb;
+  }
+  e = cudaMalloc(&ctx->bank_aT, aT.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_bT, bT.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_n2, n2.size() * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->bank_aT, aT.data(), aT.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->bank_bT, bT.data(), bT.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->bank_n2, n2.data(), n2.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    kstap_destroy(ctx);
+    return fail(nullptr, KSTAP_ECUDA, "bank upload failed: %s", cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
+                               const kstap_factors* factors) {
+  kstap_status st = check_frame(ctx, Y, H_in, W_in);
+  if (st != KSTAP_OK) return st;
+  if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
+    return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
+  const Geom g = make_geom(ctx, H_in, W_in);
+  const size_t ncell = (size_t)g.H * g.W;
+  const WsLayout L = ws_layout(g.p, ncell);
+  if (L.total > ctx->ws_bytes) {
+    if (ctx->budget && L.total > ctx->budget)
+      return fail(ctx, KSTAP_ENOMEM, "workspace %zu B exceeds the HBM budget %zu B", L.total,
+                  ctx->budget);
+    if (ctx->ws) {
+      KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      cudaFree(ctx->ws);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+    if (e != cudaSuccess)
+      return fail(ctx, KSTAP_ENOMEM, "workspace cudaMalloc(%zu) failed: %s", L.total,
+                  cudaGetErrorString(e));
+    ctx->ws_bytes = L.total;
+  }
+  const float2* Yf = (const float2*)Y;
+  switch (g.q) {
+    case 8: return launch_fit<3, 8>(ctx, g, Yf, L, factors);
+    case 16: return launch_fit<3, 16>(ctx, g, Yf, L, factors);
+    case 32: return launch_fit<3, 32>(ctx, g, Yf, L, factors);
+  }
+  return fail(ctx, KSTAP_EINVAL, "unsupported q");
+}
+
+kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
+                          const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
+                          float* T_all) {
+  kstap_status st = check_frame(ctx, Y, H_in, W_in);
+  if (st != KSTAP_OK) return st;
+  if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
+    return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
+  if (!Tmax || !vidx || !map) return fail(ctx, KSTAP_EINVAL, "Tmax, vidx and map are required");
+  const Geom g = make_geom(ctx, H_in, W_in);
+  const float2* Yf = (const float2*)Y;
+  switch (g.q) {
+    case 8: return launch_detect<3, 8>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
+    case 16: return launch_detect<3, 16>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
+    case 32: return launch_detect<3, 32>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
+  }
+  return fail(ctx, KSTAP_EINVAL, "unsupported q");
+}
+
+kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable) {
+  if (!ctx) return KSTAP_EINVAL;
+  for (int k = 0; k < kstap_nkernels; ++k) {
+    prof_collect(ctx, k);
+    ctx->kernel_ms[k] = 0.f;
+    ctx->kernel_launches[k] = 0;
+  }
+  ctx->profile = enable != 0;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launches, int n) {
+  if (!ctx || n < 0) return KSTAP_EINVAL;
+  for (int k = 0; k < kstap_nkernels; ++k) prof_collect(ctx, k);
+  for (int k = 0; k < n && k < kstap_nkernels; ++k) {
+    if (total_ms) total_ms[k] = ctx->kernel_ms[k];
+    if (launches) launches[k] = ctx->kernel_launches[k];
+  }
+  return KSTAP_OK;
+}
+
+kstap_status kstap_destroy(kstap_ctx* ctx) {
+  if (!ctx) return KSTAP_EINVAL;
+  if (ctx->ws || ctx->bank_aT) cudaStreamSynchronize(ctx->stream);
+  for (int k = 0; k <= kstap_nkernels; ++k)
+    if (ctx->ev[k][0]) {
+      cudaEventDestroy(ctx->ev[k][0]);
+      cudaEventDestroy(ctx->ev[k][1]);
+    }
+  cudaFree(ctx->ws);
+  cudaFree(ctx->bank_aT);
+  cudaFree(ctx->bank_bT);
+  cudaFree(ctx->bank_n2);
+  delete ctx;
+  return KSTAP_OK;
+}
+
+const char* kstap_last_error(const kstap_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

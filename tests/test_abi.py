@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/kstap.h declares, and rejects bad parameters before touching a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1604_03622_b300 as K
+from paper_1604_03622_b300 import build as kbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(kstap_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    kbuild.build()
+    L = K.lib()
+    names = declared_functions()
+    assert "kstap_create" in names and "kstap_detect" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_create_rejects_unsupported_parameters_without_gpu():
+    bad = [
+        K.make_params(4, 16, 1, 3, 4, 7, 1, 2, 10.0),    # p != 3
+        K.make_params(3, 12, 1, 3, 4, 7, 1, 2, 10.0),    # q not in {8,16,32}
+        K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0),    # r_a != 1
+        K.make_params(3, 8, 1, 8, 3, 4, 1, 2, 10.0),     # r_b >= q (Sec. 5)
+        K.make_params(3, 16, 1, 5, 4, 7, 1, 2, 10.0),    # r_b > 4
+        K.make_params(3, 16, 1, 3, 1, 7, 2, 2, 10.0),    # guard > ring
+        K.make_params(3, 16, 1, 3, 0, 0, 0, 0, 10.0),    # empty ring
+        K.make_params(3, 16, 1, 3, 12, 24, 1, 1, 10.0),  # box > 1024
+    ]
+    dummy = np.zeros(64, np.complex64)   # never dereferenced: validation fails first
+    for prm in bad:
+        with pytest.raises(K.KstapError, match="EINVAL"):
+            K.kstap_create(prm, _Fake(dummy), _Fake(dummy), 8)
+        assert K.kstap_last_error(None) != ""
+
+
+def test_workspace_size_formula():
+    prm = K.make_params(3, 16, 1, 3, 4, 7, 1, 2, 10.0)
+    H, W = 1024, 1024
+    b = K.kstap_workspace_bytes(prm, H + 8, W + 14 + 15)
+    per_cell = (45 + 9 + 9) * 8
+    assert per_cell * H * W <= b <= per_cell * H * W + 4096
+    assert K.kstap_workspace_bytes(prm, 5, 5) == 0
+
+
+class _Fake:
+    """Stands in for a device tensor: only data_ptr() is read."""
+
+    def __init__(self, arr):
+        self.arr = arr
+
+    def data_ptr(self):
+        return self.arr.ctypes.data
