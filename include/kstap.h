@@ -151,6 +151,31 @@ enum {
 kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable);
 kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launches, int n);
 
+/* Allocation-free variant of kstap_fit_project.  The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * while they run -- for example a real-time processing loop, where cudaMalloc
+ * may synchronise the device and has unbounded latency, or a host whose
+ * device memory is entirely owned by another allocator.  It needs no context
+ * and calls no cudaMalloc, cudaFree or other allocating routine; the caller
+ * passes the frame Y (device) and the factor arrays exactly as for
+ * kstap_fit_project, and cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).
+ *
+ * Scratch (frame scale, per-cell moments and flip-flop factors, 504 B per
+ * cell) lives in one statically allocated device array of about 16.5 MB that
+ * every GPU which loads the library holds until the process exits.  Frames
+ * with more than 32768 cells (H * W) are rejected with KSTAP_EINVAL and a
+ * message from kstap_last_error(NULL); other errors are reported the same way.
+ *
+ * The first call on each device looks up that device's address of the array
+ * (with that device current); make that first call before any stream
+ * capture.  Every call shares the one array: calls that overlap on the GPU
+ * (different streams, or different host threads, on the same device) race
+ * and corrupt each other's results, so serialise them.  The array keeps the
+ * last call's contents; the call clears what it needs zeroed itself. */
+kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y, int H_in,
+                                       int W_in, const kstap_factors* factors, void* cuda_stream);
+
 /* Bytes of workspace kstap_fit_project needs for an H_in x W_in frame with
  * these parameters (0 on invalid input). */
 size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in);

@@ -20,7 +20,7 @@ STATUS = {0: "KSTAP_OK", -1: "KSTAP_EINVAL", -2: "KSTAP_ENOMEM", -3: "KSTAP_ECUD
 
 EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
             "kstap_last_error", "kstap_workspace_bytes", "kstap_set_profiling",
-            "kstap_kernel_times"]
+            "kstap_kernel_times", "kstap_fit_project_noalloc"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -62,10 +62,12 @@ def lib() -> ctypes.CDLL:
         L.kstap_last_error.restype = ctypes.c_char_p
         L.kstap_workspace_bytes.argtypes = [ctypes.POINTER(KstapParams), I, I]
         L.kstap_workspace_bytes.restype = Z
+        L.kstap_fit_project_noalloc.argtypes = [ctypes.POINTER(KstapParams), P, I, I,
+                                                ctypes.POINTER(KstapFactors), P]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
         for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
-                     "kstap_set_profiling", "kstap_kernel_times"):
+                     "kstap_set_profiling", "kstap_kernel_times", "kstap_fit_project_noalloc"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -134,3 +136,10 @@ def kstap_kernel_times(ctx: int):
     cnt = (ctypes.c_int32 * n)()
     _check(lib().kstap_kernel_times(ctx, ms, cnt, n), ctx)
     return {KERNELS[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+
+def kstap_fit_project_noalloc(params: KstapParams, Y, H_in: int, W_in: int,
+                              factors: KstapFactors, stream: int = 0) -> None:
+    """Allocation-free fit (no context, static device scratch, <= 32768 cells)."""
+    _check(lib().kstap_fit_project_noalloc(ctypes.byref(params), _ptr(Y), H_in, W_in,
+                                           ctypes.byref(factors), stream or None))

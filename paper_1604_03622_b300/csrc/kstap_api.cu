@@ -460,3 +460,144 @@ const char* kstap_last_error(const kstap_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free fit (kstap_fit_project_noalloc).  Its scratch -- the frame
+// scale word and the per-cell moments M, block sums and flip-flop factor a --
+// lives in this file-scope device array instead of a cudaMalloc'd workspace.
+// Host code must not pass the array's name to a kernel: on the host it is only
+// a stand-in symbol.  The device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+#define KSTAP_NOALLOC_MAX_CELLS 32768
+#define KSTAP_NOALLOC_SCRATCH_BYTES (256 + (size_t)KSTAP_NOALLOC_MAX_CELLS * (45 + 9 + 9) * 8 + 1024)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KSTAP_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up on
+// the first call per device).
+kstap_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess)
+    return fail(nullptr, KSTAP_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(nullptr, KSTAP_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(nullptr, KSTAP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KSTAP_OK;
+}
+
+Geom noalloc_geom(const kstap_params& p, int H_in, int W_in) {
+  Geom g;
+  g.p = p.p;
+  g.q = p.q;
+  g.r_a = p.r_a;
+  g.r_b = p.r_b;
+  g.Rr = p.ring_r;
+  g.Ra = p.ring_a;
+  g.Gr = p.guard_r;
+  g.Ga = p.guard_a;
+  g.H_in = H_in;
+  g.W_in = W_in;
+  g.H = H_in - 2 * p.ring_r;
+  g.W = W_in - 2 * p.ring_a - p.q + 1;
+  const long nbox = (2L * p.ring_r + 1) * (2L * p.ring_a + 1);
+  g.n = (int)(nbox - (2L * p.guard_r + 1) * (2L * p.guard_a + 1));
+  g.V = 0;
+  g.B = (61 - ceil_log2(nbox)) / 2;
+  if (g.B > 26) g.B = 26;
+  g.max_iter = p.max_iter > 0 ? p.max_iter : 64;
+  g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
+  g.tau = p.tau;
+  g.tc = (p.q >= 32) ? 16 : kstap::kTileCells;
+  return g;
+}
+
+template <int P, int Q>
+kstap_status launch_fit_noalloc(const Geom& g, const float2* Y, char* scratch, const WsLayout& L,
+                                const kstap_factors* f, cudaStream_t s) {
+  unsigned* maxbits = (unsigned*)(scratch + L.flags);
+  float2* Mw = (float2*)(scratch + L.Mw);
+  float2* Sw = (float2*)(scratch + L.Sw);
+  float2* aw = (float2*)(scratch + L.aw);
+  const size_t ncell = (size_t)g.H * g.W;
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, 8, s);   // the scale words must start at zero
+  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  const size_t nfloat = 2 * (size_t)g.p * g.H_in * g.W_in;
+  int blocks = (int)std::min<size_t>((nfloat + 1023) / 1024, 148 * 16);
+  if (blocks < 1) blocks = 1;
+  kstap::k_frame_maxabs<<<blocks, 256, 0, s>>>((const float*)Y, nfloat, maxbits, maxbits + 1);
+  const size_t sm1 = smem_moments(g);
+  e = cudaFuncSetAttribute(kstap::k_moments<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm1);
+  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells, g.H);
+  kstap::k_moments<P, Q><<<grid1, kstap::kThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
+  kstap::k_flipflop<P><<<(unsigned)((ncell + 127) / 128), 128, 0, s>>>(
+      Mw, Sw, g, ncell, aw, (float2*)f->UA, f->lamA, f->iters, f->eta);
+  const size_t sm3 = smem_bfit(g);
+  e = cudaFuncSetAttribute(kstap::k_bfit<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm3);
+  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
+  kstap::k_bfit<P, Q><<<grid3, kstap::kThreads, sm3, s>>>(
+      Y, g, maxbits, aw, (float2*)f->UB_hi, (float2*)f->UB_lo, f->lamB);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return KSTAP_OK;
+}
+
+}  // namespace
+
+extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y,
+                                                  int H_in, int W_in,
+                                                  const kstap_factors* factors,
+                                                  void* cuda_stream) {
+  std::string why;
+  if (!valid_params(params, why)) return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
+  if (!Y) return fail(nullptr, KSTAP_EINVAL, "Y is NULL");
+  if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
+    return fail(nullptr, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
+  if (H_in < 2 * params->ring_r + 1 || W_in < 2 * params->ring_a + params->q)
+    return fail(nullptr, KSTAP_EINVAL, "frame %dx%d smaller than the training box plus window",
+                H_in, W_in);
+  const Geom g = noalloc_geom(*params, H_in, W_in);
+  const size_t ncell = (size_t)g.H * g.W;
+  if (ncell > KSTAP_NOALLOC_MAX_CELLS)
+    return fail(nullptr, KSTAP_EINVAL,
+                "frame has %zu cells; kstap_fit_project_noalloc handles at most %d cells "
+                "(use kstap_fit_project, or split the frame into tiles)",
+                ncell, KSTAP_NOALLOC_MAX_CELLS);
+  const WsLayout L = ws_layout(g.p, ncell);
+  if (L.total > KSTAP_NOALLOC_SCRATCH_BYTES)
+    return fail(nullptr, KSTAP_EINVAL, "scratch layout %zu B exceeds the static %zu B", L.total,
+                (size_t)KSTAP_NOALLOC_SCRATCH_BYTES);
+  void* scratch = nullptr;
+  kstap_status st = noalloc_scratch(&scratch);
+  if (st != KSTAP_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const float2* Yf = (const float2*)Y;
+  switch (g.q) {
+    case 8: return launch_fit_noalloc<3, 8>(g, Yf, (char*)scratch, L, factors, s);
+    case 16: return launch_fit_noalloc<3, 16>(g, Yf, (char*)scratch, L, factors, s);
+    case 32: return launch_fit_noalloc<3, 32>(g, Yf, (char*)scratch, L, factors, s);
+  }
+  return fail(nullptr, KSTAP_EINVAL, "unsupported q");
+}
