@@ -187,95 +187,105 @@ WsLayout ws_layout(int p, size_t ncell) {
 }
 
 size_t smem_moments(const Geom& g) {
-  const int P = g.p, PP = P * P, NE = PP * (PP + 1) / 2, TC = kstap::kTileCells;
-  const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + g.q - 1, NUmax = TC + g.q - 1;
-  size_t b = (size_t)P * NR * WT * 8;
+  const int P = g.p, PP = P * P, TC = kstap::kTileCells, TR = kstap::kMomRows;
+  const int NRT = 2 * g.Rr + TR, WT = TC + 2 * g.Ra + g.q - 1, NUmax = TC + g.q - 1;
+  size_t b = (size_t)P * NRT * WT * 8;
   b += (b & 15);
   b += 2 * (size_t)PP * WT * 16;
-  b += (size_t)PP * NUmax * 8;
-  b += (size_t)TC * NE * 8 + (size_t)TC * PP * 8;
+  b += (size_t)TR * PP * NUmax * 8;
   return b;
 }
 
 size_t smem_bfit(const Geom& g) {
-  const int P = g.p, PP = P * P, Q = g.q, TC = g.tc;
+  const int P = g.p, PP = P * P, Q = g.q, TC = g.tc, R = g.r_b;
   const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
   size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
   b += (size_t)TC * PP * 8;
-  b += (size_t)(kstap::kThreads / 32) * Q * kstap::kRbMax * 8;
-  b += (size_t)PP * NUmax * 16;
-  b += 2 * (size_t)PP * WT * 16;
+  // the eigen phase's basis scratch reuses the (then dead) lag and box-sum buffers
+  const size_t vs = (size_t)(kstap::kThreads / 32) * (32 / Q) * Q * R * 8;
+  const size_t lagb = (size_t)PP * NUmax * 16 + 2 * (size_t)PP * WT * 16;
+  b += std::max(vs, lagb);
   b += (size_t)P * NR * WT * 8;
   return b;
 }
 
 size_t smem_detect(const Geom& g) {
-  const int P = g.p, Q = g.q, V = g.V;
-  const size_t WS = (size_t)P * Q + 2 * (size_t)Q * kstap::kRbMax + 2 * P;
-  return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + (kstap::kThreads / 32) * WS * 8;
+  const int P = g.p, Q = g.q, V = g.V, R = g.r_b;
+  const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 2 * (size_t)P * R;
+  const size_t cells = (kstap::kThreads / 32) * (32 / Q);
+  return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8;
 }
 
-template <int P, int Q>
-kstap_status launch_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, const WsLayout& L,
-                        const kstap_factors* f) {
-  char* ws = (char*)ctx->ws;
-  unsigned* maxbits = (unsigned*)(ws + L.flags);
-  float2* Mw = (float2*)(ws + L.Mw);
-  float2* Sw = (float2*)(ws + L.Sw);
-  float2* aw = (float2*)(ws + L.aw);
+// Enqueues the fit (scale, moments, flip-flop, B / U_B) on stream s with the
+// given scratch; ctx (may be NULL) receives errors and profiling events.
+template <int P, int Q, int R>
+kstap_status enqueue_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
+                         const WsLayout& L, const kstap_factors* f, cudaStream_t s) {
+  unsigned* maxbits = (unsigned*)(scratch + L.flags);
+  float2* Mw = (float2*)(scratch + L.Mw);
+  float2* Sw = (float2*)(scratch + L.Sw);
+  float2* aw = (float2*)(scratch + L.aw);
   const size_t ncell = (size_t)g.H * g.W;
-  cudaStream_t s = ctx->stream;
-  KSTAP_CUDA(ctx, cudaMemsetAsync(maxbits, 0, 8, s));
+  KSTAP_CUDA(ctx, cudaMemsetAsync(maxbits, 0, 8, s));   // the scale words must start at zero
   const size_t nfloat = 2 * (size_t)g.p * g.H_in * g.W_in;
   int blocks = (int)std::min<size_t>((nfloat + 1023) / 1024, 148 * 16);
   if (blocks < 1) blocks = 1;
-  prof_collect(ctx, KSTAP_K_SCALE);
-  prof_begin(ctx, KSTAP_K_SCALE);
+  if (ctx) prof_collect(ctx, KSTAP_K_SCALE), prof_begin(ctx, KSTAP_K_SCALE);
   kstap::k_frame_maxabs<<<blocks, 256, 0, s>>>((const float*)Y, nfloat, maxbits, maxbits + 1);
-  prof_end(ctx, KSTAP_K_SCALE);
+  if (ctx) prof_end(ctx, KSTAP_K_SCALE);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
   const size_t sm1 = smem_moments(g);
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_moments<P, Q>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells, g.H);
-  prof_collect(ctx, KSTAP_K_MOMENTS);
-  prof_begin(ctx, KSTAP_K_MOMENTS);
-  kstap::k_moments<P, Q><<<grid1, kstap::kThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
-  prof_end(ctx, KSTAP_K_MOMENTS);
+  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells,
+             (g.H + kstap::kMomRows - 1) / kstap::kMomRows);
+  if (ctx) prof_collect(ctx, KSTAP_K_MOMENTS), prof_begin(ctx, KSTAP_K_MOMENTS);
+  kstap::k_moments<P, Q><<<grid1, kstap::kMomThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
+  if (ctx) prof_end(ctx, KSTAP_K_MOMENTS);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
-  prof_collect(ctx, KSTAP_K_FLIPFLOP);
-  prof_begin(ctx, KSTAP_K_FLIPFLOP);
+  if (ctx) prof_collect(ctx, KSTAP_K_FLIPFLOP), prof_begin(ctx, KSTAP_K_FLIPFLOP);
   kstap::k_flipflop<P><<<(unsigned)((ncell + 127) / 128), 128, 0, s>>>(
       Mw, Sw, g, ncell, aw, (float2*)f->UA, f->lamA, f->iters, f->eta);
-  prof_end(ctx, KSTAP_K_FLIPFLOP);
+  if (ctx) prof_end(ctx, KSTAP_K_FLIPFLOP);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
   const size_t sm3 = smem_bfit(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_bfit<P, Q>,
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_bfit<P, Q, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
-  prof_collect(ctx, KSTAP_K_BFIT);
-  prof_begin(ctx, KSTAP_K_BFIT);
-  kstap::k_bfit<P, Q><<<grid3, kstap::kThreads, sm3, s>>>(
+  if (ctx) prof_collect(ctx, KSTAP_K_BFIT), prof_begin(ctx, KSTAP_K_BFIT);
+  kstap::k_bfit<P, Q, R><<<grid3, kstap::kThreads, sm3, s>>>(
       Y, g, maxbits, aw, (float2*)f->UB_hi, (float2*)f->UB_lo, f->lamB);
-  prof_end(ctx, KSTAP_K_BFIT);
+  if (ctx) prof_end(ctx, KSTAP_K_BFIT);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;
 }
 
-template <int P, int Q>
+kstap_status dispatch_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
+                          const WsLayout& L, const kstap_factors* f, cudaStream_t s) {
+#define KSTAP_FIT(QQ, RR) \
+  if (g.q == QQ && g.r_b == RR) return enqueue_fit<3, QQ, RR>(ctx, g, Y, scratch, L, f, s);
+  KSTAP_FIT(8, 1) KSTAP_FIT(8, 2) KSTAP_FIT(8, 3) KSTAP_FIT(8, 4)
+  KSTAP_FIT(16, 1) KSTAP_FIT(16, 2) KSTAP_FIT(16, 3) KSTAP_FIT(16, 4)
+  KSTAP_FIT(32, 1) KSTAP_FIT(32, 2) KSTAP_FIT(32, 3) KSTAP_FIT(32, 4)
+#undef KSTAP_FIT
+  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
+}
+
+template <int P, int Q, int R>
 kstap_status launch_detect(kstap_ctx* ctx, const Geom& g, const float2* Y, const kstap_factors* f,
                            float* Tmax, int32_t* vidx, uint8_t* map, float* T_all) {
   const size_t ncell = (size_t)g.H * g.W;
   const size_t sm = smem_detect(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q>,
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const unsigned grid = (unsigned)((ncell + 7) / 8);
+  const size_t per_block = (kstap::kThreads / 32) * (32 / Q);
+  const unsigned grid = (unsigned)((ncell + per_block - 1) / per_block);
   prof_collect(ctx, KSTAP_K_DETECT);
   prof_begin(ctx, KSTAP_K_DETECT);
-  kstap::k_detect<P, Q><<<grid, kstap::kThreads, sm, ctx->stream>>>(
+  kstap::k_detect<P, Q, R><<<grid, kstap::kThreads, sm, ctx->stream>>>(
       Y, g, ctx->bank_aT, ctx->bank_bT, ctx->bank_n2, (const float2*)f->UA,
       (const float2*)f->UB_hi, (const float2*)f->UB_lo, Tmax, vidx, map, T_all);
   prof_end(ctx, KSTAP_K_DETECT);
@@ -391,13 +401,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
                   cudaGetErrorString(e));
     ctx->ws_bytes = L.total;
   }
-  const float2* Yf = (const float2*)Y;
-  switch (g.q) {
-    case 8: return launch_fit<3, 8>(ctx, g, Yf, L, factors);
-    case 16: return launch_fit<3, 16>(ctx, g, Yf, L, factors);
-    case 32: return launch_fit<3, 32>(ctx, g, Yf, L, factors);
-  }
-  return fail(ctx, KSTAP_EINVAL, "unsupported q");
+  return dispatch_fit(ctx, g, (const float2*)Y, (char*)ctx->ws, L, factors, ctx->stream);
 }
 
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
@@ -410,11 +414,13 @@ kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
   if (!Tmax || !vidx || !map) return fail(ctx, KSTAP_EINVAL, "Tmax, vidx and map are required");
   const Geom g = make_geom(ctx, H_in, W_in);
   const float2* Yf = (const float2*)Y;
-  switch (g.q) {
-    case 8: return launch_detect<3, 8>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
-    case 16: return launch_detect<3, 16>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
-    case 32: return launch_detect<3, 32>(ctx, g, Yf, factors, Tmax, vidx, map, T_all);
-  }
+#define KSTAP_DET(QQ, RR)                                                                 \
+  if (g.q == QQ && g.r_b == RR) return launch_detect<3, QQ, RR>(ctx, g, Yf, factors, Tmax, vidx, \
+                                                                map, T_all);
+  KSTAP_DET(8, 1) KSTAP_DET(8, 2) KSTAP_DET(8, 3) KSTAP_DET(8, 4)
+  KSTAP_DET(16, 1) KSTAP_DET(16, 2) KSTAP_DET(16, 3) KSTAP_DET(16, 4)
+  KSTAP_DET(32, 1) KSTAP_DET(32, 2) KSTAP_DET(32, 3) KSTAP_DET(32, 4)
+#undef KSTAP_DET
   return fail(ctx, KSTAP_EINVAL, "unsupported q");
 }
 
@@ -530,40 +536,6 @@ Geom noalloc_geom(const kstap_params& p, int H_in, int W_in) {
   return g;
 }
 
-template <int P, int Q>
-kstap_status launch_fit_noalloc(const Geom& g, const float2* Y, char* scratch, const WsLayout& L,
-                                const kstap_factors* f, cudaStream_t s) {
-  unsigned* maxbits = (unsigned*)(scratch + L.flags);
-  float2* Mw = (float2*)(scratch + L.Mw);
-  float2* Sw = (float2*)(scratch + L.Sw);
-  float2* aw = (float2*)(scratch + L.aw);
-  const size_t ncell = (size_t)g.H * g.W;
-  cudaError_t e = cudaMemsetAsync(maxbits, 0, 8, s);   // the scale words must start at zero
-  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-  const size_t nfloat = 2 * (size_t)g.p * g.H_in * g.W_in;
-  int blocks = (int)std::min<size_t>((nfloat + 1023) / 1024, 148 * 16);
-  if (blocks < 1) blocks = 1;
-  kstap::k_frame_maxabs<<<blocks, 256, 0, s>>>((const float*)Y, nfloat, maxbits, maxbits + 1);
-  const size_t sm1 = smem_moments(g);
-  e = cudaFuncSetAttribute(kstap::k_moments<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm1);
-  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells, g.H);
-  kstap::k_moments<P, Q><<<grid1, kstap::kThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
-  kstap::k_flipflop<P><<<(unsigned)((ncell + 127) / 128), 128, 0, s>>>(
-      Mw, Sw, g, ncell, aw, (float2*)f->UA, f->lamA, f->iters, f->eta);
-  const size_t sm3 = smem_bfit(g);
-  e = cudaFuncSetAttribute(kstap::k_bfit<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm3);
-  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
-  kstap::k_bfit<P, Q><<<grid3, kstap::kThreads, sm3, s>>>(
-      Y, g, maxbits, aw, (float2*)f->UB_hi, (float2*)f->UB_lo, f->lamB);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(nullptr, KSTAP_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
-  return KSTAP_OK;
-}
-
 }  // namespace
 
 extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y,
@@ -592,12 +564,6 @@ extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, co
   void* scratch = nullptr;
   kstap_status st = noalloc_scratch(&scratch);
   if (st != KSTAP_OK) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  const float2* Yf = (const float2*)Y;
-  switch (g.q) {
-    case 8: return launch_fit_noalloc<3, 8>(g, Yf, (char*)scratch, L, factors, s);
-    case 16: return launch_fit_noalloc<3, 16>(g, Yf, (char*)scratch, L, factors, s);
-    case 32: return launch_fit_noalloc<3, 32>(g, Yf, (char*)scratch, L, factors, s);
-  }
-  return fail(nullptr, KSTAP_EINVAL, "unsupported q");
+  return dispatch_fit(nullptr, g, (const float2*)Y, (char*)scratch, L, factors,
+                      (cudaStream_t)cuda_stream);
 }

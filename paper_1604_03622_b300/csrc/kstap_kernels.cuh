@@ -204,62 +204,198 @@ __device__ __forceinline__ void ll_to_ff(long long v, float& hi, float& lo) {
   lo = __ll2float_rn(rest) * kLagNorm;
 }
 
+// Horizontal ring sums for a chunk of up to 8 consecutive positions u0.. of
+// one plane, as exact running sums: L(u) = L(u-1) + Vo(u+2Ra) - Vo(u-1)
+// - Vg(u+Ra+Ga) + Vg(u-1+Ra-Ga).  Calls emit(u, L) for each position.
+template <typename F>
+__device__ __forceinline__ void ring_sums_run(const longlong2* __restrict__ Vo,
+                                              const longlong2* __restrict__ Vg, const Geom& g,
+                                              int u0, int u1, F&& emit) {
+  longlong2 L = ring_sum(Vo, Vg, g, u0);
+  emit(u0, L);
+  for (int u = u0 + 1; u < u1; ++u) {
+    // window [u, u + 2Ra] gains column u + 2Ra and loses u - 1; the guard
+    // window [u + Ra - Ga, u + Ra + Ga] gains u + Ra + Ga and loses u - 1 + Ra - Ga
+    const longlong2 a = Vo[u + 2 * g.Ra], b = Vo[u - 1];
+    const longlong2 c = Vg[u + g.Ra + g.Ga], d = Vg[u - 1 + g.Ra - g.Ga];
+    L.x += a.x - b.x - c.x + d.x;
+    L.y += a.y - b.y - c.y + d.y;
+    emit(u, L);
+  }
+}
+
+constexpr int kMomRows = 4;                         // cell rows per CTA in the moments pass
+constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
+constexpr int kRunChunk = 8;                        // horizontal running-sum chunk
+
 // ------------------------------------------------ K1a: lag moments ---------
-// CTA = (cell row r, tile of kTileCells cells).  Output per cell:
-//   Mw[cell][tri(J, J')]  (PP(PP+1)/2 complex) : M = R R^H, in 2^-60 L units
-//   Sw[cell][J]                                : sum of all S(i,k) entries (A_0 ~ this)
+// CTA = kMomRows cell rows x kTileCells cells, one thread per cell.
+// Output per cell (struct of arrays, element-major: X[e * ncell + cell]):
+//   Mw[e]  e < PP(PP+1)/2 : M = R R^H upper triangle, in 2^-60 L units
+//   Sw[J]                 : sum of the entries of block S(i, k) (A_0 ~ this)
+// Lags run g = Q-1 .. 0.  Before lag 0 each thread folds in the negative lags:
+// W <- W + conj(Pi W Pi^T), s <- s + conj(Pi s) (linear, so per-thread partial
+// sums may be folded before they are complete).
 template <int P, int Q>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kMomThreads)
 k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
           float2* __restrict__ Mw, float2* __restrict__ Sw) {
   constexpr int PP = P * P;
   constexpr int NE = PP * (PP + 1) / 2;
   constexpr int TC = kTileCells;
-  constexpr int TPC = kThreads / TC;   // threads per cell
+  constexpr int TR = kMomRows;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int r = blockIdx.y;
+  const int r0 = blockIdx.y * TR;
   const int c0 = blockIdx.x * TC;
   const int WT = TC + 2 * g.Ra + Q - 1;
   const int NR = 2 * g.Rr + 1;
+  const int NRT = NR + TR - 1;
   const int NUmax = TC + Q - 1;
-  int2* Yq = reinterpret_cast<int2*>(smem);
-  longlong2* Vo = reinterpret_cast<longlong2*>(Yq + P * NR * WT + (P * NR * WT & 1));
-  longlong2* Vg = Vo + PP * WT;
-  float2* lag = reinterpret_cast<float2*>(Vg + PP * WT);
-  float2* W0s = lag + PP * NUmax;          // [TC][NE]
-  float2* S0s = W0s + TC * NE;             // [TC][PP]
+  int2* Yq = reinterpret_cast<int2*>(smem);                                  // [P][NRT][WT]
+  longlong2* Vo = reinterpret_cast<longlong2*>(Yq + P * NRT * WT + (P * NRT * WT & 1));
+  longlong2* Vg = Vo + PP * WT;                                             // [PP][WT]
+  float2* lag = reinterpret_cast<float2*>(Vg + PP * WT);                    // [TR][PP][NUmax]
 
   const int sh = frame_shift(*maxbits, g.B);
   const float scale = ldexpf(1.f, sh);
-  load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
+  {
+    const int total = P * NRT * WT;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int col = idx % WT;
+      const int rho = (idx / WT) % NRT;
+      const int i = idx / (WT * NRT);
+      const int gr = r0 + rho, gc = c0 + col;
+      int2 v = make_int2(0, 0);
+      if (gc < g.W_in && gr < g.H_in) {
+        const float2 y = __ldg(Y + ((size_t)i * g.H_in + gr) * g.W_in + gc);
+        v.x = quantise(y.x, scale);
+        v.y = quantise(y.y, scale);
+      }
+      Yq[idx] = v;
+    }
+  }
   __syncthreads();
 
-  const int cl = threadIdx.x / TPC;
-  const int t = threadIdx.x % TPC;
-  const bool live = (c0 + cl) < g.W;
-
+  const int tr = threadIdx.x / TC, cl = threadIdx.x % TC;
+  const bool live = (c0 + cl) < g.W && (r0 + tr) < g.H;
   float wr[NE], wi[NE], sr[PP], si[PP];
 #pragma unroll
   for (int e = 0; e < NE; ++e) wr[e] = wi[e] = 0.f;
 #pragma unroll
   for (int J = 0; J < PP; ++J) sr[J] = si[J] = 0.f;
 
-  for (int lagg = 0; lagg < Q; ++lagg) {
+  const int g0 = g.Rr - g.Gr, g1 = g.Rr + g.Gr;
+  for (int lagg = Q - 1; lagg >= 0; --lagg) {
     const int NU = TC + Q - 1 - lagg;
     const int KW = NU + 2 * g.Ra;
-    vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
-      const int u = idx % NU, J = idx / NU;
-      const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
-      lag[J * NUmax + u] = make_float2(__ll2float_rn(L.x) * kLagNorm, __ll2float_rn(L.y) * kLagNorm);
+    for (int t = 0; t < TR; ++t) {
+      // vertical ring sums of cell row t: direct for t = 0, running after
+      for (int idx = threadIdx.x; idx < PP * KW; idx += blockDim.x) {
+        const int kap = idx % KW, J = idx / KW;
+        const int i = J % P, k = J / P;
+        const int2* yi = Yq + (size_t)i * NRT * WT + kap;
+        const int2* yk = Yq + (size_t)k * NRT * WT + kap + lagg;
+        auto prod = [&](int rho, long long& pr, long long& pim) {
+          const int2 a = yi[rho * WT], b = yk[rho * WT];
+          pr = (long long)a.x * b.x + (long long)a.y * b.y;
+          pim = (long long)a.y * b.x - (long long)a.x * b.y;
+        };
+        long long pr, pim;
+        longlong2 vo, vg;
+        if (t == 0) {
+          vo = make_longlong2(0, 0);
+          vg = make_longlong2(0, 0);
+          for (int rho = 0; rho < NR; ++rho) {
+            prod(rho, pr, pim);
+            vo.x += pr;
+            vo.y += pim;
+            if (rho >= g0 && rho <= g1) {
+              vg.x += pr;
+              vg.y += pim;
+            }
+          }
+        } else {
+          vo = Vo[J * KW + kap];
+          vg = Vg[J * KW + kap];
+          prod(t - 1 + NR, pr, pim);
+          vo.x += pr;
+          vo.y += pim;
+          prod(t - 1, pr, pim);
+          vo.x -= pr;
+          vo.y -= pim;
+          prod(t + g1, pr, pim);
+          vg.x += pr;
+          vg.y += pim;
+          prod(t - 1 + g0, pr, pim);
+          vg.x -= pr;
+          vg.y -= pim;
+        }
+        Vo[J * KW + kap] = vo;
+        Vg[J * KW + kap] = vg;
+      }
+      __syncthreads();
+      const int nch = (NU + kRunChunk - 1) / kRunChunk;
+      for (int idx = threadIdx.x; idx < PP * nch; idx += blockDim.x) {
+        const int ch = idx % nch, J = idx / nch;
+        float2* out = lag + ((size_t)t * PP + J) * NUmax;
+        ring_sums_run(Vo + J * KW, Vg + J * KW, g, ch * kRunChunk,
+                      min(NU, (ch + 1) * kRunChunk), [&](int u, longlong2 L) {
+                        out[u] = make_float2(__ll2float_rn(L.x) * kLagNorm,
+                                             __ll2float_rn(L.y) * kLagNorm);
+                      });
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    if (lagg == 0) {
+      // fold the negative lags: W += conj(Pi W Pi^T), s += conj(Pi s)
+#pragma unroll
+      for (int J = 0; J < PP; ++J) {
+#pragma unroll
+        for (int Jp = J; Jp < PP; ++Jp) {
+          const int a = (J % P) * P + (J / P), b = (Jp % P) * P + (Jp / P);
+          const int e = tri_idx(PP, J, Jp);
+          const int ep = (a <= b) ? tri_idx(PP, a, b) : tri_idx(PP, b, a);
+          if (ep < e) continue;                 // each pair once
+          if (ep == e) {
+            // conj(W[pi J, pi J']) with the same storage slot
+            const float xr = wr[e], xi = (a <= b) ? wi[e] : -wi[e];
+            wr[e] += xr;
+            wi[e] -= xi;
+          } else {
+            // slot e receives conj(W[a,b]); slot ep receives conj(W[pi a, pi b]) = conj(W[J,J'] or its conj)
+            const float er = wr[e], ei = wi[e], fr = wr[ep], fi = wi[ep];
+            const float abr = fr, abi = (a <= b) ? fi : -fi;    // W[a, b]
+            wr[e] = er + abr;
+            wi[e] = ei - abi;
+            // slot ep holds W[min(a,b), max(a,b)]; pi maps (a,b) back to (J,J')
+            const float jr = er, ji = (a <= b) ? ei : -ei;      // W[pi a, pi b] in ep's orientation
+            wr[ep] = fr + jr;
+            wi[ep] = fi - ji;
+          }
+        }
+      }
+#pragma unroll
+      for (int J = 0; J < PP; ++J) {
+        const int a = (J % P) * P + (J / P);
+        if (a < J) continue;
+        if (a == J) {
+          si[J] = 0.f;                             // s_J + conj(s_J) is real
+          sr[J] *= 2.f;
+        } else {
+          const float xr = sr[J], xi = si[J], yr = sr[a], yi = si[a];
+          sr[J] = xr + yr;
+          si[J] = xi - yi;
+          sr[a] = yr + xr;
+          si[a] = yi - xi;
+        }
+      }
+    }
     if (live) {
-      for (int j = t; j < Q - lagg; j += TPC) {
+      const float2* lt = lag + (size_t)tr * PP * NUmax;
+      for (int j = 0; j < Q - lagg; ++j) {
         float2 l[PP];
 #pragma unroll
-        for (int J = 0; J < PP; ++J) l[J] = lag[J * NUmax + cl + j];
+        for (int J = 0; J < PP; ++J) l[J] = lt[J * NUmax + cl + j];
 #pragma unroll
         for (int J = 0; J < PP; ++J) {
           sr[J] += l[J].x;
@@ -267,89 +403,21 @@ k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ max
 #pragma unroll
           for (int Jp = J; Jp < PP; ++Jp) {
             const int e = tri_idx(PP, J, Jp);
-            // l[J] conj(l[Jp])
-            wr[e] += l[J].x * l[Jp].x + l[J].y * l[Jp].y;
+            wr[e] += l[J].x * l[Jp].x + l[J].y * l[Jp].y;   // l[J] conj(l[J'])
             wi[e] += l[J].y * l[Jp].x - l[J].x * l[Jp].y;
           }
         }
       }
     }
-    if (lagg == 0) {
-      // reduce W_0 over the TPC threads of the cell, park it in shared memory
-#pragma unroll
-      for (int e = 0; e < NE; ++e) {
-#pragma unroll
-        for (int o = TPC / 2; o > 0; o >>= 1) {
-          wr[e] += __shfl_xor_sync(0xffffffffu, wr[e], o);
-          wi[e] += __shfl_xor_sync(0xffffffffu, wi[e], o);
-        }
-      }
-#pragma unroll
-      for (int J = 0; J < PP; ++J) {
-#pragma unroll
-        for (int o = TPC / 2; o > 0; o >>= 1) {
-          sr[J] += __shfl_xor_sync(0xffffffffu, sr[J], o);
-          si[J] += __shfl_xor_sync(0xffffffffu, si[J], o);
-        }
-      }
-      if (t == 0) {
-#pragma unroll
-        for (int e = 0; e < NE; ++e) W0s[cl * NE + e] = make_float2(wr[e], wi[e]);
-#pragma unroll
-        for (int J = 0; J < PP; ++J) S0s[cl * PP + J] = make_float2(sr[J], si[J]);
-      }
-#pragma unroll
-      for (int e = 0; e < NE; ++e) wr[e] = wi[e] = 0.f;
-#pragma unroll
-      for (int J = 0; J < PP; ++J) sr[J] = si[J] = 0.f;
-    }
     __syncthreads();
   }
-  // reduce W_{>0}
+  if (live) {
+    const size_t ncell = (size_t)g.H * g.W;
+    const size_t cell = (size_t)(r0 + tr) * g.W + (c0 + cl);
 #pragma unroll
-  for (int e = 0; e < NE; ++e) {
+    for (int e = 0; e < NE; ++e) Mw[e * ncell + cell] = make_float2(wr[e], wi[e]);
 #pragma unroll
-    for (int o = TPC / 2; o > 0; o >>= 1) {
-      wr[e] += __shfl_xor_sync(0xffffffffu, wr[e], o);
-      wi[e] += __shfl_xor_sync(0xffffffffu, wi[e], o);
-    }
-  }
-#pragma unroll
-  for (int J = 0; J < PP; ++J) {
-#pragma unroll
-    for (int o = TPC / 2; o > 0; o >>= 1) {
-      sr[J] += __shfl_xor_sync(0xffffffffu, sr[J], o);
-      si[J] += __shfl_xor_sync(0xffffffffu, si[J], o);
-    }
-  }
-  if (t == 0 && live) {
-    const size_t cell = (size_t)r * g.W + (c0 + cl);
-    // M[J,J'] = W0 + Wp + conj(Wp[pi J, pi J'])
-#pragma unroll
-    for (int J = 0; J < PP; ++J) {
-#pragma unroll
-      for (int Jp = J; Jp < PP; ++Jp) {
-        const int e = tri_idx(PP, J, Jp);
-        const int a = (J % P) * P + (J / P);     // pi(J): (i,k) -> (k,i)
-        const int b = (Jp % P) * P + (Jp / P);
-        float pr, pim;                           // Wp[a, b]
-        if (a <= b) {
-          pr = wr[tri_idx(PP, a, b)];
-          pim = wi[tri_idx(PP, a, b)];
-        } else {
-          pr = wr[tri_idx(PP, b, a)];
-          pim = -wi[tri_idx(PP, b, a)];
-        }
-        const float2 w0 = W0s[cl * NE + e];
-        Mw[cell * NE + e] = make_float2(w0.x + wr[e] + pr, w0.y + wi[e] - pim);
-      }
-    }
-#pragma unroll
-    for (int J = 0; J < PP; ++J) {
-      const int a = (J % P) * P + (J / P);
-      const float2 s0 = S0s[cl * PP + J];
-      Sw[cell * PP + J] = make_float2(s0.x + sr[J] + sr[a], s0.y + si[J] - si[a]);
-    }
+    for (int J = 0; J < PP; ++J) Sw[J * ncell + cell] = make_float2(sr[J], si[J]);
   }
 }
 
@@ -448,10 +516,10 @@ k_flipflop(const float2* __restrict__ Mw, const float2* __restrict__ Sw, Geom g,
   if (cell >= ncell) return;
   float2 M[NE];
 #pragma unroll
-  for (int e = 0; e < NE; ++e) M[e] = Mw[cell * NE + e];
+  for (int e = 0; e < NE; ++e) M[e] = Mw[e * ncell + cell];
   float2 a[PP];
 #pragma unroll
-  for (int J = 0; J < PP; ++J) a[J] = Sw[cell * PP + J];
+  for (int J = 0; J < PP; ++J) a[J] = Sw[J * ncell + cell];
   // a_0 = R 1 / q^2 is proportional to the sum of S's block entries; Hermitise.
 #pragma unroll
   for (int i = 0; i < P; ++i)
@@ -540,7 +608,7 @@ k_flipflop(const float2* __restrict__ Mw, const float2* __restrict__ Sw, Geom g,
     aMa += (double)a[J].x * sr + (double)a[J].y * si;
   }
 #pragma unroll
-  for (int J = 0; J < PP; ++J) aw[cell * PP + J] = a[J];
+  for (int J = 0; J < PP; ++J) aw[J * ncell + cell] = a[J];
   float trA = 0.f;
 #pragma unroll
   for (int m = 0; m < P; ++m)
@@ -564,42 +632,234 @@ k_flipflop(const float2* __restrict__ Mw, const float2* __restrict__ Sw, Geom g,
 }
 
 // ------------------------------------------------ K3: B and U_B ------------
-// Reads B(j, l) of one cell from the float-float upper triangle (by diagonal).
+// B(j, l) of one cell, float-float upper triangle stored by diagonal:
+// diagonal d = l - j >= 0 at offset d*Q - d(d-1)/2, entry j.  float4 =
+// (re_hi, re_lo, im_hi, im_lo).  Lower entries are conjugates.
+template <int Q>
+__host__ __device__ constexpr int diag_off(int d) { return d * Q - (d * (d - 1)) / 2; }
+
 template <int Q>
 __device__ __forceinline__ float4 b_at(const float4* __restrict__ Bc, int j, int l) {
-  // Bc layout: diagonal d = l - j >= 0 at offset d*Q - d(d-1)/2, entry j
-  if (l >= j) {
-    const int d = l - j;
-    return Bc[d * Q - (d * (d - 1)) / 2 + j];
-  }
-  const int d = j - l;
-  const float4 v = Bc[d * Q - (d * (d - 1)) / 2 + l];
-  return make_float4(v.x, v.y, -v.z, -v.w);   // conj: (re_hi, re_lo, im_hi, im_lo)
+  if (l >= j) return Bc[diag_off<Q>(l - j) + j];
+  const float4 v = Bc[diag_off<Q>(j - l) + l];
+  return make_float4(v.x, v.y, -v.z, -v.w);
 }
 
-template <int P, int Q>
-__device__ void eig_top_subspace(const float4* __restrict__ Bc, const Geom& g, int lane,
-                                 float2 (&uh)[kRbMax], float2 (&ul)[kRbMax], float (&lam)[kRbMax],
-                                 float2* __restrict__ Vs);
+// Row j of B times the q x R matrix Vs ([l][R]), visiting l = (j + t) mod Q so
+// that the Q lanes of a group read consecutive shared-memory words.
+template <int Q, int R>
+__device__ __forceinline__ void b_times_v_fp32(const float4* __restrict__ Bc, int j,
+                                               const float2* __restrict__ Vs, float2 (&y)[R]) {
+#pragma unroll
+  for (int m = 0; m < R; ++m) y[m] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int t = 0; t < Q; ++t) {
+    const int l = (j + t) & (Q - 1);
+    const float4 b = b_at<Q>(Bc, j, l);
+    const float2 bh = make_float2(b.x, b.z);
+#pragma unroll
+    for (int m = 0; m < R; ++m) y[m] = cadd(y[m], cmul(bh, Vs[l * R + m]));
+  }
+}
 
-template <int P, int Q>
+template <int G>
+__device__ __forceinline__ float grp_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ float2 grp_sum2(float2 v) {
+  return make_float2(grp_sum<G>(v.x), grp_sum<G>(v.y));
+}
+template <int G>
+__device__ __forceinline__ ff grp_sum_ff(ff v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    ff w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_add(v, w);
+  }
+  return v;
+}
+
+// Modified Gram-Schmidt over the Q lanes of a group (FP32).
+template <int Q, int R>
+__device__ __forceinline__ void orthonormalise_g(float2 (&x)[R]) {
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+#pragma unroll
+    for (int mp = 0; mp < m; ++mp) {
+      const float2 cc = grp_sum2<Q>(cmulc(x[mp], x[m]));
+      x[m] = csub(x[m], cmul(x[mp], cc));
+    }
+    const float nrm = sqrtf(grp_sum<Q>(cabs2(x[m])));
+    x[m] = cscale(x[m], nrm > 0.f ? 1.f / nrm : 0.f);
+  }
+}
+
+// Leading R-dimensional eigenspace of one cell's B (group of Q lanes, lane j
+// = row j): FP32 subspace iteration on B_hi until the invariant-subspace
+// residual |BV - V V^H B V| <= 2e-6 |BV| (all cells of the warp), then
+// float-float subspace steps Y = B V with Cholesky-QR; a second step runs
+// only while the first still moved the subspace by > 1e-6.  Loop exits are
+// warp-uniform because several cells share a warp.  `live` = this group's
+// cell exists; dead groups compute on zeros.
+template <int Q, int R>
+__device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live,
+                                 float2* __restrict__ Vs, float2 (&uh)[R], float2 (&ul)[R],
+                                 float (&lam)[R]) {
+  float2 v[R], y[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const float4 b = b_at<Q>(Bc, j, ((2 * m + 1) * Q) / (2 * R));
+    v[m] = make_float2(b.x, b.z);
+  }
+  orthonormalise_g<Q, R>(v);
+  for (int it = 0; it < 48; ++it) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+    __syncwarp();
+    b_times_v_fp32<Q, R>(Bc, j, Vs, y);
+    __syncwarp();
+    float ry = 0.f, re = 0.f;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      float2 e = y[m];
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp) e = csub(e, cmul(v[mp], grp_sum2<Q>(cmulc(v[mp], y[m]))));
+      ry += cabs2(y[m]);
+      re += cabs2(e);
+    }
+    ry = grp_sum<Q>(ry);
+    re = grp_sum<Q>(re);
+    orthonormalise_g<Q, R>(y);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = y[m];
+    const bool done = !live || re <= 4e-12f * ry || !(ry > 0.f);
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  // Ritz values (FP32) for reporting: eigenvalues of V^H B V
+  {
+#pragma unroll
+    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+    __syncwarp();
+    float2 bv[R];
+    b_times_v_fp32<Q, R>(Bc, j, Vs, bv);
+    __syncwarp();
+    float2 Gm[R][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp) Gm[m][mp] = grp_sum2<Q>(cmulc(v[m], bv[mp]));
+    float dd[R];
+    float2 UU[R][R];
+    jacobi_small<R>(Gm, dd, UU);
+#pragma unroll
+    for (int m = 0; m < R; ++m) lam[m] = dd[m];
+  }
+  cff U[R];
+  for (int step = 0; step < 3; ++step) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+    __syncwarp();
+    float s[R][4];
+#pragma unroll
+    for (int m = 0; m < R; ++m) s[m][0] = s[m][1] = s[m][2] = s[m][3] = 0.f;
+#pragma unroll 2
+    for (int t = 0; t < Q; ++t) {
+      const int l = (j + t) & (Q - 1);
+      const float4 b = b_at<Q>(Bc, j, l);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const float2 x = Vs[l * R + m];
+        acc_ffxf(s[m][0], s[m][1], b.x, b.y, x.x);     // re = br xr - bi xi
+        acc_ffxf(s[m][0], s[m][1], b.z, b.w, -x.y);
+        acc_ffxf(s[m][2], s[m][3], b.x, b.y, x.y);     // im = br xi + bi xr
+        acc_ffxf(s[m][2], s[m][3], b.z, b.w, x.x);
+      }
+    }
+    __syncwarp();
+    cff Yf[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) Yf[m] = cff{ff_make(s[m][0], s[m][1]), ff_make(s[m][2], s[m][3])};
+    // Gram G = Y^H Y, Cholesky G = L L^H, U = Y L^-H (float-float)
+    cff Gm[R][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+      for (int mp = m; mp < R; ++mp) {
+        const cff pr = cff_cmul(Yf[m], Yf[mp]);
+        Gm[m][mp] = cff{grp_sum_ff<Q>(pr.re), grp_sum_ff<Q>(pr.im)};
+      }
+    cff L[R][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      ff dsum = Gm[m][m].re;
+#pragma unroll
+      for (int k = 0; k < m; ++k)
+        dsum = ff_sub(dsum, ff_add(ff_mul(L[m][k].re, L[m][k].re), ff_mul(L[m][k].im, L[m][k].im)));
+      const ff lmm = ff_sqrt(dsum);
+      L[m][m] = cff{lmm, {0.f, 0.f}};
+#pragma unroll
+      for (int i = m + 1; i < R; ++i) {
+        cff t = cff{Gm[m][i].re, ff_neg(Gm[m][i].im)};
+#pragma unroll
+        for (int k = 0; k < m; ++k) t = cff_sub(t, cff_mul(L[i][k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
+        L[i][m] = cff{ff_div(t.re, lmm), ff_div(t.im, lmm)};
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      cff t = Yf[m];
+#pragma unroll
+      for (int k = 0; k < m; ++k) t = cff_sub(t, cff_mul(U[k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
+      const ff lmm = L[m][m].re;
+      U[m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
+    }
+    // change of the subspace in this step: |U - V V^H U|_F (single precision)
+    float change = 0.f;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const float2 um = make_float2(U[m].re.hi, U[m].im.hi);
+      float2 e = um;
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp) e = csub(e, cmul(v[mp], grp_sum2<Q>(cmulc(v[mp], um))));
+      change += cabs2(e);
+    }
+    change = grp_sum<Q>(change);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
+    const bool done = !live || change < 1e-12f;
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    uh[m] = make_float2(U[m].re.hi, U[m].im.hi);
+    ul[m] = make_float2(U[m].re.lo, U[m].im.lo);
+  }
+}
+
+template <int P, int Q, int R>
 __global__ void __launch_bounds__(kThreads)
 k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
        const float2* __restrict__ aw, float2* __restrict__ UBh, float2* __restrict__ UBl,
        float* __restrict__ lamB) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
+  constexpr int CPW = 32 / Q;   // cells per warp in the eigen phase
   extern __shared__ __align__(16) unsigned char smem[];
   const int TC = g.tc;
   const int r = blockIdx.y;
   const int c0 = blockIdx.x * TC;
   const int WT = TC + 2 * g.Ra + Q - 1;
-  const int NR = 2 * g.Rr + 1;
   const int NUmax = TC + Q - 1;
+  const size_t ncell = (size_t)g.H * g.W;
   float4* Bs = reinterpret_cast<float4*>(smem);                 // [TC][NB]
   float2* as = reinterpret_cast<float2*>(Bs + TC * NB);         // [TC][PP]
-  float2* Vs = as + TC * PP;                                    // [warps][Q][kRbMax]
-  float4* lag = reinterpret_cast<float4*>(Vs + (kThreads / 32) * Q * kRbMax);   // [PP][NUmax]
+  float4* lag = reinterpret_cast<float4*>(as + TC * PP);        // [PP][NUmax]
+  float2* Vs = reinterpret_cast<float2*>(lag);                  // eigen phase: [warps * CPW][Q][R]
   longlong2* Vo = reinterpret_cast<longlong2*>(lag + PP * NUmax);
   longlong2* Vg = Vo + PP * WT;
   int2* Yq = reinterpret_cast<int2*>(Vg + PP * WT);
@@ -610,7 +870,7 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
   for (int idx = threadIdx.x; idx < TC * PP; idx += blockDim.x) {
     const int cl = idx / PP, J = idx % PP;
     const int c = c0 + cl;
-    as[idx] = (c < g.W) ? aw[((size_t)r * g.W + c) * PP + J] : make_float2(0.f, 0.f);
+    as[idx] = (c < g.W) ? aw[J * ncell + (size_t)r * g.W + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
 
@@ -619,13 +879,17 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
     const int KW = NU + 2 * g.Ra;
     vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
-      const int u = idx % NU, J = idx / NU;
-      const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
-      float4 v;
-      ll_to_ff(L.x, v.x, v.y);
-      ll_to_ff(L.y, v.z, v.w);
-      lag[J * NUmax + u] = v;
+    const int nch = (NU + kRunChunk - 1) / kRunChunk;
+    for (int idx = threadIdx.x; idx < PP * nch; idx += blockDim.x) {
+      const int ch = idx % nch, J = idx / nch;
+      float4* out = lag + J * NUmax;
+      ring_sums_run(Vo + J * KW, Vg + J * KW, g, ch * kRunChunk, min(NU, (ch + 1) * kRunChunk),
+                    [&](int u, longlong2 L) {
+                      float4 v;
+                      ll_to_ff(L.x, v.x, v.y);
+                      ll_to_ff(L.y, v.z, v.w);
+                      out[u] = v;
+                    });
     }
     __syncthreads();
     // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float
@@ -637,452 +901,242 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
       for (int J = 0; J < PP; ++J) {
         const float2 a = as[cl * PP + J];
         const float4 L = lag[J * NUmax + cl + j];
-        // conj(a) * L = (a.x L.re + a.y L.im) + i (a.x L.im - a.y L.re)
-        acc_ffxf(sr, cr, L.x, L.y, a.x);
+        acc_ffxf(sr, cr, L.x, L.y, a.x);     // conj(a) L: re = ar Lr + ai Li
         acc_ffxf(sr, cr, L.z, L.w, a.y);
-        acc_ffxf(si, ci, L.z, L.w, a.x);
+        acc_ffxf(si, ci, L.z, L.w, a.x);     //            im = ar Li - ai Lr
         acc_ffxf(si, ci, L.x, L.y, -a.y);
       }
       const ff re = ff_make(sr, cr), im = ff_make(si, ci);
-      Bs[cl * NB + lagg * Q - (lagg * (lagg - 1)) / 2 + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      Bs[cl * NB + diag_off<Q>(lagg) + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
     __syncthreads();
   }
 
-  // eigen phase: one warp per cell
+  // eigen phase: a group of Q lanes per cell
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int cl = warp; cl < TC; cl += kThreads / 32) {
-    const int c = c0 + cl;
-    if (c >= g.W) break;
-    float2 uh[kRbMax], ul[kRbMax];
-    float lam[kRbMax];
-    eig_top_subspace<P, Q>(Bs + cl * NB, g, lane, uh, ul, lam, Vs + warp * Q * kRbMax);
-    const size_t cell = (size_t)r * g.W + c;
-    if (lane < Q) {
-      for (int m = 0; m < g.r_b; ++m) {
-        UBh[(cell * Q + lane) * g.r_b + m] = uh[m];
-        UBl[(cell * Q + lane) * g.r_b + m] = ul[m];
+  const int sub = lane / Q, j = lane % Q;
+  const int slot = warp * CPW + sub;
+  const int per_pass = (kThreads / 32) * CPW;
+  for (int base = 0; base < TC; base += per_pass) {
+    const int cl = base + slot;
+    const bool live = cl < TC && (c0 + cl) < g.W;
+    const int clc = live ? cl : 0;
+    float2 uh[R], ul[R];
+    float lam[R];
+    eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
+    if (live) {
+      const size_t cell = (size_t)r * g.W + (c0 + cl);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        UBh[(cell * Q + j) * R + m] = uh[m];
+        UBl[(cell * Q + j) * R + m] = ul[m];
+      }
+      if (j == 0 && lamB) {
+        // B^ = b / |a|^2 in S units, then tr A^ = p normalisation
+        float an = 0.f, tr = 0.f;
+        for (int J = 0; J < PP; ++J) an += cabs2(as[cl * PP + J]);
+        for (int i = 0; i < P; ++i) tr += as[cl * PP + i * (P + 1)].x;
+        const float unit = ldexpf(1.f, 60 - 2 * sh) / (float)g.n;
+        const float f = (an > 0.f) ? unit / an * tr / (float)P : 0.f;
+#pragma unroll
+        for (int m = 0; m < R; ++m) lamB[cell * R + m] = lam[m] * f;
       }
     }
-    if (lane == 0 && lamB) {
-      // B^ = b / |a|^2 in S units, then tr A^ = p normalisation
-      float an = 0.f, tr = 0.f;
-      for (int J = 0; J < PP; ++J) an += cabs2(as[cl * PP + J]);
-      for (int i = 0; i < P; ++i) tr += as[cl * PP + i * (P + 1)].x;
-      const float unit = ldexpf(1.f, 60 - 2 * frame_shift(*maxbits, g.B)) / (float)g.n;
-      const float f = (an > 0.f) ? unit / an * tr / (float)P : 0.f;
-      for (int m = 0; m < g.r_b; ++m) lamB[cell * g.r_b + m] = lam[m] * f;
-    }
-  }
-}
-
-// FP32 subspace iteration on B_hi, then float-float steps (Cholesky-QR) on
-// the full B.  Lane j < Q owns row j of the q x r_b basis.
-template <int P, int Q>
-__device__ void eig_top_subspace(const float4* __restrict__ Bc, const Geom& g, int lane,
-                                 float2 (&uh)[kRbMax], float2 (&ul)[kRbMax], float (&lam)[kRbMax],
-                                 float2* __restrict__ Vs) {
-  const int R = g.r_b;
-  const bool row = lane < Q;
-  float2 v[kRbMax], y[kRbMax];
-  // start: r_b columns of B spread over the window
-#pragma unroll
-  for (int m = 0; m < kRbMax; ++m) {
-    v[m] = make_float2(0.f, 0.f);
-    if (m < R && row) {
-      const float4 b = b_at<Q>(Bc, lane, ((2 * m + 1) * Q) / (2 * R));
-      v[m] = make_float2(b.x, b.z);
-    }
-  }
-  auto orthonormalise = [&](float2 (&x)[kRbMax]) {
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) break;
-#pragma unroll
-      for (int mp = 0; mp < kRbMax; ++mp) {
-        if (mp >= m) break;
-        const float2 cc = warp_sum2(cmulc(x[mp], x[m]));
-        x[m] = csub(x[m], cmul(x[mp], cc));
-      }
-      const float nrm = sqrtf(warp_sum(cabs2(x[m])));
-      const float inv = (nrm > 0.f) ? 1.f / nrm : 0.f;
-      x[m] = cscale(x[m], inv);
-    }
-  };
-  orthonormalise(v);
-  // FP32 subspace iteration until the residual |BV - V V^H B V| / |BV| is small
-  for (int it = 0; it < 64; ++it) {
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m)
-      if (row) Vs[lane * kRbMax + m] = v[m];
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) y[m] = make_float2(0.f, 0.f);
-    if (row) {
-      for (int l = 0; l < Q; ++l) {
-        const float4 b = b_at<Q>(Bc, lane, l);
-        const float2 bh = make_float2(b.x, b.z);
-#pragma unroll
-        for (int m = 0; m < kRbMax; ++m) y[m] = cadd(y[m], cmul(bh, Vs[l * kRbMax + m]));
-      }
-    }
-    __syncwarp();
-    // residual
-    float ry = 0.f, re = 0.f;
-    float2 e[kRbMax];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) e[m] = y[m];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) break;
-#pragma unroll
-      for (int mp = 0; mp < kRbMax; ++mp) {
-        if (mp >= R) break;
-        const float2 gmm = warp_sum2(cmulc(v[mp], y[m]));
-        e[m] = csub(e[m], cmul(v[mp], gmm));
-      }
-      ry += cabs2(y[m]);
-      re += cabs2(e[m]);
-    }
-    ry = warp_sum(ry);
-    re = warp_sum(re);
-    orthonormalise(y);
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) v[m] = y[m];
-    if (re <= 1e-12f * ry) break;
-  }
-  // Rayleigh-Ritz values (FP32) for reporting: eigenvalues of V^H B V
-  {
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m)
-      if (row) Vs[lane * kRbMax + m] = v[m];
-    __syncwarp();
-    float2 G[kRbMax][kRbMax];
-    float2 bv[kRbMax];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) bv[m] = make_float2(0.f, 0.f);
-    if (row) {
-      for (int l = 0; l < Q; ++l) {
-        const float4 b = b_at<Q>(Bc, lane, l);
-        const float2 bh = make_float2(b.x, b.z);
-#pragma unroll
-        for (int m = 0; m < kRbMax; ++m) bv[m] = cadd(bv[m], cmul(bh, Vs[l * kRbMax + m]));
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m)
-#pragma unroll
-      for (int mp = 0; mp < kRbMax; ++mp)
-        G[m][mp] = (m < R && mp < R) ? warp_sum2(cmulc(v[m], bv[mp]))
-                                     : make_float2(0.f, 0.f);
-    float dd[kRbMax];
-    float2 UU[kRbMax][kRbMax];
-    jacobi_small<kRbMax>(G, dd, UU);
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) lam[m] = dd[m];
-  }
-  // float-float subspace steps: Y = B V (FF), Cholesky-QR in FF
-  cff U[kRbMax];
-  for (int step = 0; step < 3; ++step) {
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m)
-      if (row) Vs[lane * kRbMax + m] = v[m];
-    __syncwarp();
-    float s[kRbMax][4];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) s[m][0] = s[m][1] = s[m][2] = s[m][3] = 0.f;
-    if (row) {
-      for (int l = 0; l < Q; ++l) {
-        const float4 b = b_at<Q>(Bc, lane, l);
-#pragma unroll
-        for (int m = 0; m < kRbMax; ++m) {
-          const float2 x = Vs[l * kRbMax + m];
-          // (br + i bi)(xr + i xi): re = br xr - bi xi, im = br xi + bi xr
-          acc_ffxf(s[m][0], s[m][1], b.x, b.y, x.x);
-          acc_ffxf(s[m][0], s[m][1], b.z, b.w, -x.y);
-          acc_ffxf(s[m][2], s[m][3], b.x, b.y, x.y);
-          acc_ffxf(s[m][2], s[m][3], b.z, b.w, x.x);
-        }
-      }
-    }
-    __syncwarp();
-    cff Yf[kRbMax];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) Yf[m] = cff{ff_make(s[m][0], s[m][1]), ff_make(s[m][2], s[m][3])};
-    // Gram G = Y^H Y (FF), Cholesky G = L L^H, U = Y L^-H
-    cff G[kRbMax][kRbMax];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m)
-#pragma unroll
-      for (int mp = m; mp < kRbMax; ++mp) {
-        if (m < R && mp < R) {
-          const cff pr = cff_cmul(Yf[m], Yf[mp]);
-          G[m][mp] = cff{ff_warp_sum(pr.re), ff_warp_sum(pr.im)};
-        } else {
-          G[m][mp] = cff_zero();
-        }
-      }
-    cff L[kRbMax][kRbMax];
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) break;
-      ff dsum = G[m][m].re;
-#pragma unroll
-      for (int k = 0; k < kRbMax; ++k) {
-        if (k >= m) break;
-        dsum = ff_sub(dsum, ff_add(ff_mul(L[m][k].re, L[m][k].re), ff_mul(L[m][k].im, L[m][k].im)));
-      }
-      const ff lmm = ff_sqrt(dsum);
-      L[m][m] = cff{lmm, {0.f, 0.f}};
-#pragma unroll
-      for (int i = 0; i < kRbMax; ++i) {
-        if (i <= m || i >= R) continue;
-        // L[i][m] = (G[i][m] - sum_k L[i][k] conj(L[m][k])) / L[m][m];  G[i][m] = conj(G[m][i])
-        cff t = cff{G[m][i].re, ff_neg(G[m][i].im)};
-#pragma unroll
-        for (int k = 0; k < kRbMax; ++k) {
-          if (k >= m) break;
-          t = cff_sub(t, cff_mul(L[i][k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
-        }
-        L[i][m] = cff{ff_div(t.re, lmm), ff_div(t.im, lmm)};
-      }
-    }
-    float change = 0.f;
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) {
-        U[m] = cff_zero();
-        continue;
-      }
-      cff t = Yf[m];
-#pragma unroll
-      for (int k = 0; k < kRbMax; ++k) {
-        if (k >= m) break;
-        // Y[:, m] = sum_{k <= m} U[:, k] conj(L[m][k])
-        t = cff_sub(t, cff_mul(U[k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
-      }
-      const ff lmm = L[m][m].re;
-      U[m] = cff{ff_div(t.re, lmm), ff_div(t.im, lmm)};
-      if (!row) U[m] = cff_zero();
-    }
-    // change of the subspace: |U - V V^H U|_F (single precision estimate)
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) break;
-      float2 um = make_float2(U[m].re.hi, U[m].im.hi);
-      float2 e = um;
-#pragma unroll
-      for (int mp = 0; mp < kRbMax; ++mp) {
-        if (mp >= R) break;
-        const float2 cc = warp_sum2(cmulc(v[mp], um));
-        e = csub(e, cmul(v[mp], cc));
-      }
-      change += cabs2(e);
-    }
-    change = warp_sum(change);
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
-    if (step >= 1 && change < 1e-12f) break;
-  }
-#pragma unroll
-  for (int m = 0; m < kRbMax; ++m) {
-    uh[m] = make_float2(U[m].re.hi, U[m].im.hi);
-    ul[m] = make_float2(U[m].re.lo, U[m].im.lo);
   }
 }
 
 // ------------------------------------------------ K4: detect ---------------
-// One warp per cell.  Bank in shared memory, transposed: bT[j * V + v].
-template <int P, int Q>
+// A group of Q lanes per cell (32/Q cells per warp).  Per cell:
+//   C  = X conj(U_B)                 (P x R, float-float; one lane per (i, m))
+//   Z1 = X - C U_B^T = X F_B^T       (float-float, rounded; lane j owns column j)
+//   Z  = F_A Z1                      (FP32)
+// Bank (lanes over v, 4 velocities per pass):
+//   w_b = F_B b_v = b_v - U_B (U_B^H b_v),  w_a = F_A a_v     (FP32)
+//   T_v = |w_a^H Z conj(w_b)|^2 / (|w_a|^2 |w_b|^2)
+// which equals |d^H P x|^2 / (d^H P d) since P Z = Z.  Computing the
+// numerator with the projected steering factors keeps it well conditioned
+// when d_v lies close to the clutter subspace; with Z float-float accurate,
+// the error of T_v is ~2 eps sqrt(q) / sqrt(d^H P d / |d|^2).
+template <int P, int Q, int R>
 __global__ void __launch_bounds__(kThreads)
 k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_aT,
          const float2* __restrict__ bank_bT, const float* __restrict__ bank_n2,
          const float2* __restrict__ UA, const float2* __restrict__ UBh,
          const float2* __restrict__ UBl, float* __restrict__ Tmax, int32_t* __restrict__ vidx,
          uint8_t* __restrict__ map, float* __restrict__ T_all) {
+  constexpr int G = Q;                         // lanes per cell
+  constexpr int CPW = 32 / G;                  // cells per warp
+  constexpr int CPB = (kThreads / 32) * CPW;   // cells per block
+  constexpr int VB = 4;                        // velocities per lane per pass
+  constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 2 * P * R;   // float2 scratch per cell
   extern __shared__ __align__(16) unsigned char smem[];
   const int V = g.V;
   float2* aT = reinterpret_cast<float2*>(smem);       // [P][V]
   float2* bT = aT + P * V;                             // [Q][V]
   float* na = reinterpret_cast<float*>(bT + Q * V);    // [V]
   float* nb = na + V;                                  // [V]
-  constexpr int WS = P * Q + 2 * Q * kRbMax + P * 2;   // per-warp float2 scratch
-  float2* wsp = reinterpret_cast<float2*>(na + 2 * V);  // 8V bytes past an 8-aligned start
+  float2* scr = reinterpret_cast<float2*>(na + 2 * V);
   for (int i = threadIdx.x; i < P * V; i += blockDim.x) aT[i] = bank_aT[i];
   for (int i = threadIdx.x; i < Q * V; i += blockDim.x) bT[i] = bank_bT[i];
   for (int i = threadIdx.x; i < 2 * V; i += blockDim.x) na[i] = bank_n2[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t cell = (size_t)blockIdx.x * (kThreads / 32) + warp;
+  const int sub = lane / G, gl = lane % G;
+  const int slot = warp * CPW + sub;
+  const size_t cell = (size_t)blockIdx.x * CPB + slot;
   const size_t ncell = (size_t)g.H * g.W;
-  if (cell >= ncell) return;
-  float2* Zs = wsp + warp * WS;              // [P][Q]
-  float2* Us = Zs + P * Q;                   // [Q][kRbMax] hi
-  float2* Ul = Us + Q * kRbMax;              // [Q][kRbMax] lo
-  float2* Uas = Ul + Q * kRbMax;             // [P] (r_a = 1 columns; P * r_a <= 2P)
-  const int r = (int)(cell / g.W), c = (int)(cell % g.W);
-  const int R = g.r_b;
-  const bool row = lane < Q;
-  // X column `lane`, U_B row `lane`
-  float2 x[P];
-  float2 uh[kRbMax], ul[kRbMax];
+  const bool live = cell < ncell;
+  float2* Xs = scr + slot * CS;        // [P][Q]
+  float2* Zs = Xs + P * Q;             // [P][Q]
+  float2* Uh = Zs + P * Q;             // [Q][R]
+  float2* Ul = Uh + Q * R;             // [Q][R]
+  float2* Ua = Ul + Q * R;             // [P]   (r_a = 1)
+  float4* Cs = reinterpret_cast<float4*>(Ua + 2 * P);   // [P][R] float-float complex
+  if (live) {
+    const int r = (int)(cell / g.W), c = (int)(cell % g.W);
 #pragma unroll
-  for (int i = 0; i < P; ++i)
-    x[i] = row ? __ldg(Y + ((size_t)i * g.H_in + (r + g.Rr)) * g.W_in + (c + g.Ra + lane))
-               : make_float2(0.f, 0.f);
+    for (int i = 0; i < P; ++i)
+      Xs[i * Q + gl] = __ldg(Y + ((size_t)i * g.H_in + (r + g.Rr)) * g.W_in + (c + g.Ra + gl));
 #pragma unroll
-  for (int m = 0; m < kRbMax; ++m) {
-    uh[m] = (row && m < R) ? UBh[(cell * Q + lane) * R + m] : make_float2(0.f, 0.f);
-    ul[m] = (row && m < R) ? UBl[(cell * Q + lane) * R + m] : make_float2(0.f, 0.f);
-    if (row) {
-      Us[lane * kRbMax + m] = uh[m];
-      Ul[lane * kRbMax + m] = ul[m];
+    for (int m = 0; m < R; ++m) {
+      Uh[gl * R + m] = UBh[(cell * Q + gl) * R + m];
+      Ul[gl * R + m] = UBl[(cell * Q + gl) * R + m];
     }
+    if (gl < P) Ua[gl] = UA[cell * P + gl];
   }
-  if (lane < P * g.r_a) Uas[lane] = UA[cell * P * g.r_a + lane];
-  // C[i][m] = sum_j X[i][j] conj(U_B[j][m])  (float-float)
-  cff Cm[P][kRbMax];
-#pragma unroll
-  for (int i = 0; i < P; ++i)
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
+  __syncwarp();
+  // C[i][m] = sum_j X[i][j] conj(U[j][m]), float-float
+  if (live) {
+    for (int it = gl; it < P * R; it += G) {
+      const int i = it / R, m = it % R;
       float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-      // x * conj(u): re = xr ur + xi ui, im = xi ur - xr ui
-      acc_ffxf(sr, cr, uh[m].x, ul[m].x, x[i].x);
-      acc_ffxf(sr, cr, uh[m].y, ul[m].y, x[i].y);
-      acc_ffxf(si, ci, uh[m].x, ul[m].x, x[i].y);
-      acc_ffxf(si, ci, uh[m].y, ul[m].y, -x[i].x);
-      Cm[i][m] = cff{ff_warp_sum(ff_make(sr, cr)), ff_warp_sum(ff_make(si, ci))};
+#pragma unroll 4
+      for (int j = 0; j < Q; ++j) {
+        const float2 x = Xs[i * Q + j];
+        const float2 uh = Uh[j * R + m], ul = Ul[j * R + m];
+        acc_ffxf(sr, cr, uh.x, ul.x, x.x);    // re += ur xr + ui xi
+        acc_ffxf(sr, cr, uh.y, ul.y, x.y);
+        acc_ffxf(si, ci, uh.x, ul.x, x.y);    // im += ur xi - ui xr
+        acc_ffxf(si, ci, uh.y, ul.y, -x.x);
+      }
+      const ff re = ff_make(sr, cr), im = ff_make(si, ci);
+      Cs[i * R + m] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
-  // Z1 = X - C U_B^T (float-float), then Z = Z1 - U_A U_A^H Z1 (FP32)
-  float2 z[P];
-#pragma unroll
-  for (int i = 0; i < P; ++i) {
-    cff t = cff{{x[i].x, 0.f}, {x[i].y, 0.f}};
-#pragma unroll
-    for (int m = 0; m < kRbMax; ++m) {
-      if (m >= R) break;
-      const cff u = cff{{uh[m].x, ul[m].x}, {uh[m].y, ul[m].y}};
-      t = cff_sub(t, cff_mul(Cm[i][m], u));
-    }
-    z[i] = make_float2(__fadd_rn(t.re.hi, t.re.lo), __fadd_rn(t.im.hi, t.im.lo));
   }
   __syncwarp();
-  for (int m = 0; m < g.r_a; ++m) {
-    float2 tm = make_float2(0.f, 0.f);
+  // Z1 = X - C U^T (float-float) then Z = F_A Z1; lane gl owns column j = gl
+  if (live) {
+    const int j = gl;
+    float2 uh[R], ul[R];
 #pragma unroll
-    for (int i = 0; i < P; ++i) tm = cadd(tm, cmulc(Uas[i * g.r_a + m], z[i]));
-#pragma unroll
-    for (int i = 0; i < P; ++i) z[i] = csub(z[i], cmul(Uas[i * g.r_a + m], tm));
-  }
-  if (row)
-#pragma unroll
-    for (int i = 0; i < P; ++i) Zs[i * Q + lane] = row ? z[i] : make_float2(0.f, 0.f);
-  __syncwarp();
-  // bank: lane handles v = lane, lane + 32, ...
-  float best = -1.f;
-  int bestv = 0;
-  for (int v = lane; v < V; v += 32) {
-    // num = a_v^H Z conj(b_v)
-    float2 num = make_float2(0.f, 0.f);
+    for (int m = 0; m < R; ++m) {
+      uh[m] = Uh[j * R + m];
+      ul[m] = Ul[j * R + m];
+    }
+    float2 z[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      float2 zi = make_float2(0.f, 0.f);
+      const float2 x = Xs[i * Q + j];
+      float sr = x.x, cr = 0.f, si = x.y, ci = 0.f;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) zi = cadd(zi, cmul(Zs[i * Q + j], cconj(bT[j * V + v])));
-      num = cadd(num, cmulc(aT[i * V + v], zi));
-    }
-    // den_B = |b|^2 - sum_m |U_B[:,m]^H b|^2, den_A likewise
-    float pb = 0.f;
-    for (int m = 0; m < R; ++m) {
-      float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < Q; ++j) t = cadd(t, cmulc(Us[j * kRbMax + m], bT[j * V + v]));
-      pb += cabs2(t);
-    }
-    float pa = 0.f;
-    for (int m = 0; m < g.r_a; ++m) {
-      float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Uas[i * g.r_a + m], aT[i * V + v]));
-      pa += cabs2(t);
-    }
-    const float nav = na[v], nbv = nb[v];
-    float denA = nav - pa, denB = nbv - pb;
-    float nm = cabs2(num);
-    if (denB < kBlind * nbv || denA < kBlind * nav) {
-      // re-project the steering factors: w_b = F_B b in float-float, w_a = F_A a
-      float2 wa[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) wa[i] = aT[i * V + v];
-      for (int m = 0; m < g.r_a; ++m) {
-        float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Uas[i * g.r_a + m], aT[i * V + v]));
-#pragma unroll
-        for (int i = 0; i < P; ++i) wa[i] = csub(wa[i], cmul(Uas[i * g.r_a + m], t));
+      for (int m = 0; m < R; ++m) {
+        const float4 C = Cs[i * R + m];   // (re_hi, re_lo, im_hi, im_lo)
+        // re -= Cr Ur - Ci Ui ; im -= Cr Ui + Ci Ur
+        acc_ffxff(sr, cr, C.x, C.y, -uh[m].x, -ul[m].x);
+        acc_ffxff(sr, cr, C.z, C.w, uh[m].y, ul[m].y);
+        acc_ffxff(si, ci, C.x, C.y, -uh[m].y, -ul[m].y);
+        acc_ffxff(si, ci, C.z, C.w, -uh[m].x, -ul[m].x);
       }
-      cff tb[kRbMax];
+      z[i] = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+    }
+    float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int m = 0; m < kRbMax; ++m) {
-        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-        if (m < R) {
+    for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], z[i]));
 #pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            const float2 b = bT[j * V + v];
-            const float2 h = Us[j * kRbMax + m], l = Ul[j * kRbMax + m];
-            // conj(u) b: re = ur br + ui bi, im = ur bi - ui br
-            acc_ffxf(sr, cr, h.x, l.x, b.x);
-            acc_ffxf(sr, cr, h.y, l.y, b.y);
-            acc_ffxf(si, ci, h.x, l.x, b.y);
-            acc_ffxf(si, ci, h.y, l.y, -b.x);
+    for (int i = 0; i < P; ++i) Zs[i * Q + j] = csub(z[i], cmul(Ua[i], t));
+  }
+  __syncwarp();
+  float best = -1.f;
+  int bestv = 0x7fffffff;
+  if (live) {
+    for (int v0 = gl * VB; v0 < V; v0 += G * VB) {
+      const int nv = min(VB, V - v0);
+      float2 Gm[VB][R];
+#pragma unroll
+      for (int k = 0; k < VB; ++k)
+#pragma unroll
+        for (int m = 0; m < R; ++m) Gm[k][m] = make_float2(0.f, 0.f);
+      // G = U_B^H b_v
+#pragma unroll 4
+      for (int j = 0; j < Q; ++j) {
+        float2 u[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) u[m] = Uh[j * R + m];
+#pragma unroll
+        for (int k = 0; k < VB; ++k) {
+          if (k < nv) {
+            const float2 b = bT[j * V + v0 + k];
+#pragma unroll
+            for (int m = 0; m < R; ++m) Gm[k][m] = cadd(Gm[k][m], cmulc(u[m], b));
           }
         }
-        tb[m] = cff{ff_make(sr, cr), ff_make(si, ci)};
       }
-      float2 numw = make_float2(0.f, 0.f);
-      float dB = 0.f;
-      float2 zi[P];
+      // w_b = b - U G ; y_i = sum_j Z[i][j] conj(w_b[j]) ; dB = |w_b|^2
+      float2 y[VB][P];
+      float dB[VB];
 #pragma unroll
-      for (int i = 0; i < P; ++i) zi[i] = make_float2(0.f, 0.f);
+      for (int k = 0; k < VB; ++k) {
+        dB[k] = 0.f;
 #pragma unroll
+        for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
+      }
+#pragma unroll 4
       for (int j = 0; j < Q; ++j) {
-        const float2 b = bT[j * V + v];
-        cff w = cff{{b.x, 0.f}, {b.y, 0.f}};
+        float2 u[R], zz[P];
 #pragma unroll
-        for (int m = 0; m < kRbMax; ++m) {
-          if (m >= R) break;
-          const cff u = cff{{Us[j * kRbMax + m].x, Ul[j * kRbMax + m].x},
-                            {Us[j * kRbMax + m].y, Ul[j * kRbMax + m].y}};
-          w = cff_sub(w, cff_mul(u, tb[m]));
+        for (int m = 0; m < R; ++m) u[m] = Uh[j * R + m];
+#pragma unroll
+        for (int i = 0; i < P; ++i) zz[i] = Zs[i * Q + j];
+#pragma unroll
+        for (int k = 0; k < VB; ++k) {
+          if (k < nv) {
+            float2 w = bT[j * V + v0 + k];
+#pragma unroll
+            for (int m = 0; m < R; ++m) w = csub(w, cmul(u[m], Gm[k][m]));
+            dB[k] += cabs2(w);
+#pragma unroll
+            for (int i = 0; i < P; ++i) y[k][i] = cadd(y[k][i], cmul(zz[i], cconj(w)));
+          }
         }
-        const float2 wb = make_float2(__fadd_rn(w.re.hi, w.re.lo), __fadd_rn(w.im.hi, w.im.lo));
-        dB += cabs2(wb);
-#pragma unroll
-        for (int i = 0; i < P; ++i) zi[i] = cadd(zi[i], cmul(Zs[i * Q + j], cconj(wb)));
       }
-      float dA = 0.f;
 #pragma unroll
-      for (int i = 0; i < P; ++i) {
-        dA += cabs2(wa[i]);
-        numw = cadd(numw, cmulc(wa[i], zi[i]));
+      for (int k = 0; k < VB; ++k) {
+        if (k >= nv) break;
+        const int v = v0 + k;
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], aT[i * V + v]));
+        float dA = 0.f;
+        float2 num = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const float2 wa = csub(aT[i * V + v], cmul(Ua[i], t));
+          dA += cabs2(wa);
+          num = cadd(num, cmulc(wa, y[k][i]));
+        }
+        const float den = dA * dB[k];
+        const float T = (den < 1e-12f * na[v] * nb[v]) ? 0.f : cabs2(num) / den;
+        if (T_all) T_all[cell * V + v] = T;
+        if (T > best) {
+          best = T;
+          bestv = v;
+        }
       }
-      nm = cabs2(numw);
-      denA = dA;
-      denB = dB;
-    }
-    const float den = denA * denB;
-    const float T = (den < 1e-12f * nav * nbv) ? 0.f : nm / den;
-    if (T_all) T_all[cell * V + v] = T;
-    if (T > best) {
-      best = T;
-      bestv = v;
     }
   }
-  // warp argmax, lowest v on ties
+  // group argmax, lowest v on ties
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = G / 2; o > 0; o >>= 1) {
     const float ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int ov = __shfl_xor_sync(0xffffffffu, bestv, o);
     if (ob > best || (ob == best && ov < bestv)) {
@@ -1090,7 +1144,7 @@ k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_a
       bestv = ov;
     }
   }
-  if (lane == 0) {
+  if (live && gl == 0) {
     Tmax[cell] = best;
     vidx[cell] = bestv;
     map[cell] = (best > g.tau) ? 1 : 0;

@@ -50,6 +50,20 @@ def test_parity_full_small_frames(name, H, W):
     print(name, H, W, rep)
 
 
+@pytest.mark.parametrize("name,r_b", [("small64", 1), ("small64", 3), ("small64", 4),
+                                      ("frame1024", 1), ("frame1024", 2), ("frame1024", 4),
+                                      ("precision2048", 2), ("precision2048", 3)])
+def test_parity_every_rank_variant(name, r_b):
+    """Every (q, r_b) kernel instantiation against the oracle (clutter of rank r_b)."""
+    wl = _wl(name, 9, 37, r_b=r_b)
+    f = gen.make_frame(wl)
+    ref = oracle.run_workload(f)
+    gpu = run_gpu(f)
+    compare(gpu, ref, np.arange(wl.H * wl.W), wl.tau)
+    PB = projector(gpu["UB_hi"].astype(np.complex128) + gpu["UB_lo"])
+    assert np.abs(PB - ref["PB"]).max() < 1e-8
+
+
 def test_parity_rank_one_temporal_and_single_cell():
     wl = _wl("small64", 1, 1, r_b=1)
     f = gen.make_frame(wl)
