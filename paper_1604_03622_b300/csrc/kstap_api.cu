@@ -169,20 +169,21 @@ Geom make_geom(const kstap_ctx* ctx, int H_in, int W_in) {
   return g;
 }
 
-// workspace layout
+// workspace layout (struct of arrays per cell, plus the optional lag store)
 struct WsLayout {
-  size_t flags, Mw, Sw, aw, total;
+  size_t flags, Mw, Sw, aw, Lw, total;
 };
 
-WsLayout ws_layout(int p, size_t ncell) {
-  const size_t PP = (size_t)p * p, NE = PP * (PP + 1) / 2;
+WsLayout ws_layout(int p, int q, size_t H, size_t W, bool lag_store) {
+  const size_t PP = (size_t)p * p, NE = PP * (PP + 1) / 2, ncell = H * W;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   WsLayout L;
   L.flags = 0;
   L.Mw = 256;
   L.Sw = up(L.Mw + ncell * NE * sizeof(float2));
   L.aw = up(L.Sw + ncell * PP * sizeof(float2));
-  L.total = up(L.aw + ncell * PP * sizeof(float2));
+  L.Lw = up(L.aw + ncell * PP * sizeof(float2));
+  L.total = L.Lw + (lag_store ? up(H * q * PP * (W + q - 1) * sizeof(float4)) : 0);
   return L;
 }
 
@@ -196,16 +197,16 @@ size_t smem_moments(const Geom& g) {
   return b;
 }
 
-size_t smem_bfit(const Geom& g) {
+size_t smem_bfit(const Geom& g, bool from_store) {
   const int P = g.p, PP = P * P, Q = g.q, TC = g.tc, R = g.r_b;
   const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
   size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
   b += (size_t)TC * PP * 8;
   // the eigen phase's basis scratch reuses the (then dead) lag and box-sum buffers
   const size_t vs = (size_t)(kstap::kThreads / 32) * (32 / Q) * Q * R * 8;
-  const size_t lagb = (size_t)PP * NUmax * 16 + 2 * (size_t)PP * WT * 16;
+  const size_t lagb = (size_t)PP * NUmax * 16 + (from_store ? 0 : 2 * (size_t)PP * WT * 16);
   b += std::max(vs, lagb);
-  b += (size_t)P * NR * WT * 8;
+  if (!from_store) b += (size_t)P * NR * WT * 8;
   return b;
 }
 
@@ -220,8 +221,10 @@ size_t smem_detect(const Geom& g) {
 // given scratch; ctx (may be NULL) receives errors and profiling events.
 template <int P, int Q, int R>
 kstap_status enqueue_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
-                         const WsLayout& L, const kstap_factors* f, cudaStream_t s) {
+                         const WsLayout& L, bool lag_store, const kstap_factors* f,
+                         cudaStream_t s) {
   unsigned* maxbits = (unsigned*)(scratch + L.flags);
+  float4* Lw = lag_store ? (float4*)(scratch + L.Lw) : nullptr;
   float2* Mw = (float2*)(scratch + L.Mw);
   float2* Sw = (float2*)(scratch + L.Sw);
   float2* aw = (float2*)(scratch + L.aw);
@@ -241,7 +244,7 @@ kstap_status enqueue_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* s
   dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells,
              (g.H + kstap::kMomRows - 1) / kstap::kMomRows);
   if (ctx) prof_collect(ctx, KSTAP_K_MOMENTS), prof_begin(ctx, KSTAP_K_MOMENTS);
-  kstap::k_moments<P, Q><<<grid1, kstap::kMomThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw);
+  kstap::k_moments<P, Q><<<grid1, kstap::kMomThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw, Lw);
   if (ctx) prof_end(ctx, KSTAP_K_MOMENTS);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
@@ -251,22 +254,24 @@ kstap_status enqueue_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* s
   if (ctx) prof_end(ctx, KSTAP_K_FLIPFLOP);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
-  const size_t sm3 = smem_bfit(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_bfit<P, Q, R>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+  const size_t sm3 = smem_bfit(g, lag_store);
+  auto kb = lag_store ? kstap::k_bfit<P, Q, R, true> : kstap::k_bfit<P, Q, R, false>;
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
   if (ctx) prof_collect(ctx, KSTAP_K_BFIT), prof_begin(ctx, KSTAP_K_BFIT);
-  kstap::k_bfit<P, Q, R><<<grid3, kstap::kThreads, sm3, s>>>(
-      Y, g, maxbits, aw, (float2*)f->UB_hi, (float2*)f->UB_lo, f->lamB);
+  kb<<<grid3, kstap::kThreads, sm3, s>>>(Y, g, maxbits, aw, Lw, (float2*)f->UB_hi,
+                                          (float2*)f->UB_lo, f->lamB);
   if (ctx) prof_end(ctx, KSTAP_K_BFIT);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;
 }
 
 kstap_status dispatch_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
-                          const WsLayout& L, const kstap_factors* f, cudaStream_t s) {
-#define KSTAP_FIT(QQ, RR) \
-  if (g.q == QQ && g.r_b == RR) return enqueue_fit<3, QQ, RR>(ctx, g, Y, scratch, L, f, s);
+                          const WsLayout& L, bool lag_store, const kstap_factors* f,
+                          cudaStream_t s) {
+#define KSTAP_FIT(QQ, RR)        \
+  if (g.q == QQ && g.r_b == RR) \
+    return enqueue_fit<3, QQ, RR>(ctx, g, Y, scratch, L, lag_store, f, s);
   KSTAP_FIT(8, 1) KSTAP_FIT(8, 2) KSTAP_FIT(8, 3) KSTAP_FIT(8, 4)
   KSTAP_FIT(16, 1) KSTAP_FIT(16, 2) KSTAP_FIT(16, 3) KSTAP_FIT(16, 4)
   KSTAP_FIT(32, 1) KSTAP_FIT(32, 2) KSTAP_FIT(32, 3) KSTAP_FIT(32, 4)
@@ -315,7 +320,7 @@ size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in) {
   const long H = H_in - 2L * params->ring_r;
   const long W = W_in - 2L * params->ring_a - params->q + 1;
   if (H < 1 || W < 1) return 0;
-  return ws_layout(params->p, (size_t)H * W).total;
+  return ws_layout(params->p, params->q, (size_t)H, (size_t)W, true).total;
 }
 
 kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
@@ -384,7 +389,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
     return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
   const Geom g = make_geom(ctx, H_in, W_in);
   const size_t ncell = (size_t)g.H * g.W;
-  const WsLayout L = ws_layout(g.p, ncell);
+  const WsLayout L = ws_layout(g.p, g.q, g.H, g.W, true);
   if (L.total > ctx->ws_bytes) {
     if (ctx->budget && L.total > ctx->budget)
       return fail(ctx, KSTAP_ENOMEM, "workspace %zu B exceeds the HBM budget %zu B", L.total,
@@ -401,7 +406,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
                   cudaGetErrorString(e));
     ctx->ws_bytes = L.total;
   }
-  return dispatch_fit(ctx, g, (const float2*)Y, (char*)ctx->ws, L, factors, ctx->stream);
+  return dispatch_fit(ctx, g, (const float2*)Y, (char*)ctx->ws, L, true, factors, ctx->stream);
 }
 
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
@@ -557,13 +562,13 @@ extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, co
                 "frame has %zu cells; kstap_fit_project_noalloc handles at most %d cells "
                 "(use kstap_fit_project, or split the frame into tiles)",
                 ncell, KSTAP_NOALLOC_MAX_CELLS);
-  const WsLayout L = ws_layout(g.p, ncell);
+  const WsLayout L = ws_layout(g.p, g.q, g.H, g.W, false);
   if (L.total > KSTAP_NOALLOC_SCRATCH_BYTES)
     return fail(nullptr, KSTAP_EINVAL, "scratch layout %zu B exceeds the static %zu B", L.total,
                 (size_t)KSTAP_NOALLOC_SCRATCH_BYTES);
   void* scratch = nullptr;
   kstap_status st = noalloc_scratch(&scratch);
   if (st != KSTAP_OK) return st;
-  return dispatch_fit(nullptr, g, (const float2*)Y, (char*)scratch, L, factors,
+  return dispatch_fit(nullptr, g, (const float2*)Y, (char*)scratch, L, false, factors,
                       (cudaStream_t)cuda_stream);
 }

@@ -204,42 +204,27 @@ __device__ __forceinline__ void ll_to_ff(long long v, float& hi, float& lo) {
   lo = __ll2float_rn(rest) * kLagNorm;
 }
 
-// Horizontal ring sums for a chunk of up to 8 consecutive positions u0.. of
-// one plane, as exact running sums: L(u) = L(u-1) + Vo(u+2Ra) - Vo(u-1)
-// - Vg(u+Ra+Ga) + Vg(u-1+Ra-Ga).  Calls emit(u, L) for each position.
-template <typename F>
-__device__ __forceinline__ void ring_sums_run(const longlong2* __restrict__ Vo,
-                                              const longlong2* __restrict__ Vg, const Geom& g,
-                                              int u0, int u1, F&& emit) {
-  longlong2 L = ring_sum(Vo, Vg, g, u0);
-  emit(u0, L);
-  for (int u = u0 + 1; u < u1; ++u) {
-    // window [u, u + 2Ra] gains column u + 2Ra and loses u - 1; the guard
-    // window [u + Ra - Ga, u + Ra + Ga] gains u + Ra + Ga and loses u - 1 + Ra - Ga
-    const longlong2 a = Vo[u + 2 * g.Ra], b = Vo[u - 1];
-    const longlong2 c = Vg[u + g.Ra + g.Ga], d = Vg[u - 1 + g.Ra - g.Ga];
-    L.x += a.x - b.x - c.x + d.x;
-    L.y += a.y - b.y - c.y + d.y;
-    emit(u, L);
-  }
-}
-
 constexpr int kMomRows = 4;                         // cell rows per CTA in the moments pass
 constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
-constexpr int kRunChunk = 8;                        // horizontal running-sum chunk
 
 // ------------------------------------------------ K1a: lag moments ---------
-// CTA = kMomRows cell rows x kTileCells cells, one thread per cell.
+// CTA = kMomRows cell rows x kTileCells cells, one thread per cell.  The
+// vertical box sums run down the kMomRows rows as exact int64 running sums.
 // Output per cell (struct of arrays, element-major: X[e * ncell + cell]):
 //   Mw[e]  e < PP(PP+1)/2 : M = R R^H upper triangle, in 2^-60 L units
 //   Sw[J]                 : sum of the entries of block S(i, k) (A_0 ~ this)
 // Lags run g = Q-1 .. 0.  Before lag 0 each thread folds in the negative lags:
 // W <- W + conj(Pi W Pi^T), s <- s + conj(Pi s) (linear, so per-thread partial
 // sums may be folded before they are complete).
+// Lag store (optional, Lw != nullptr): the exact lag sums of every cell row,
+// as float-float complex (re_hi, re_lo, im_hi, im_lo), laid out
+// Lw[((row * Q + g) * PP + J) * WL + u], WL = W + Q - 1, so that the B pass
+// reads them instead of recomputing them.  Each tile writes positions
+// u in [c0, c0 + TC) (the last tile also its halo).
 template <int P, int Q>
 __global__ void __launch_bounds__(kMomThreads)
 k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
-          float2* __restrict__ Mw, float2* __restrict__ Sw) {
+          float2* __restrict__ Mw, float2* __restrict__ Sw, float4* __restrict__ Lw) {
   constexpr int PP = P * P;
   constexpr int NE = PP * (PP + 1) / 2;
   constexpr int TC = kTileCells;
@@ -334,15 +319,19 @@ k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ max
         Vg[J * KW + kap] = vg;
       }
       __syncthreads();
-      const int nch = (NU + kRunChunk - 1) / kRunChunk;
-      for (int idx = threadIdx.x; idx < PP * nch; idx += blockDim.x) {
-        const int ch = idx % nch, J = idx / nch;
-        float2* out = lag + ((size_t)t * PP + J) * NUmax;
-        ring_sums_run(Vo + J * KW, Vg + J * KW, g, ch * kRunChunk,
-                      min(NU, (ch + 1) * kRunChunk), [&](int u, longlong2 L) {
-                        out[u] = make_float2(__ll2float_rn(L.x) * kLagNorm,
-                                             __ll2float_rn(L.y) * kLagNorm);
-                      });
+      // horizontal ring sums, one thread per (plane, position): consecutive
+      // threads read consecutive shared-memory words
+      const bool last_tile = c0 + TC >= g.W;
+      const int WL = g.W + Q - 1;
+      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
+        const int u = idx % NU, J = idx / NU;
+        const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
+        float4 v;
+        ll_to_ff(L.x, v.x, v.y);
+        ll_to_ff(L.y, v.z, v.w);
+        lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
+        if (Lw && (u < TC || last_tile) && c0 + u < WL && r0 + t < g.H)
+          Lw[(((size_t)(r0 + t) * Q + lagg) * PP + J) * WL + c0 + u] = v;
       }
       __syncthreads();
     }
@@ -717,6 +706,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     v[m] = make_float2(b.x, b.z);
   }
   orthonormalise_g<Q, R>(v);
+  float2 H[R][R];   // V^H B V of the last iteration (its eigenvalues are the Ritz values)
   for (int it = 0; it < 48; ++it) {
 #pragma unroll
     for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
@@ -728,7 +718,10 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     for (int m = 0; m < R; ++m) {
       float2 e = y[m];
 #pragma unroll
-      for (int mp = 0; mp < R; ++mp) e = csub(e, cmul(v[mp], grp_sum2<Q>(cmulc(v[mp], y[m]))));
+      for (int mp = 0; mp < R; ++mp) {
+        H[mp][m] = grp_sum2<Q>(cmulc(v[mp], y[m]));
+        e = csub(e, cmul(v[mp], H[mp][m]));
+      }
       ry += cabs2(y[m]);
       re += cabs2(e);
     }
@@ -740,22 +733,12 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     const bool done = !live || re <= 4e-12f * ry || !(ry > 0.f);
     if (__all_sync(0xffffffffu, done)) break;
   }
-  // Ritz values (FP32) for reporting: eigenvalues of V^H B V
+  // Ritz values (FP32) for reporting: eigenvalues of V^H B V of the converged
+  // iteration (accurate to the square of its residual)
   {
-#pragma unroll
-    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
-    __syncwarp();
-    float2 bv[R];
-    b_times_v_fp32<Q, R>(Bc, j, Vs, bv);
-    __syncwarp();
-    float2 Gm[R][R];
-#pragma unroll
-    for (int m = 0; m < R; ++m)
-#pragma unroll
-      for (int mp = 0; mp < R; ++mp) Gm[m][mp] = grp_sum2<Q>(cmulc(v[m], bv[mp]));
     float dd[R];
     float2 UU[R][R];
-    jacobi_small<R>(Gm, dd, UU);
+    jacobi_small<R>(H, dd, UU);
 #pragma unroll
     for (int m = 0; m < R; ++m) lam[m] = dd[m];
   }
@@ -841,11 +824,14 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   }
 }
 
-template <int P, int Q, int R>
+// FROM_STORE: read the float-float lag sums written by k_moments (Lw);
+// otherwise recompute them from Y (used by the allocation-free entry point,
+// whose static scratch has no room for the lag store).
+template <int P, int Q, int R, bool FROM_STORE>
 __global__ void __launch_bounds__(kThreads)
 k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
-       const float2* __restrict__ aw, float2* __restrict__ UBh, float2* __restrict__ UBl,
-       float* __restrict__ lamB) {
+       const float2* __restrict__ aw, const float4* __restrict__ Lw, float2* __restrict__ UBh,
+       float2* __restrict__ UBl, float* __restrict__ lamB) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
   constexpr int CPW = 32 / Q;   // cells per warp in the eigen phase
@@ -866,7 +852,7 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
 
   const int sh = frame_shift(*maxbits, g.B);
   const float scale = ldexpf(1.f, sh);
-  load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
+  if (!FROM_STORE) load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
   for (int idx = threadIdx.x; idx < TC * PP; idx += blockDim.x) {
     const int cl = idx / PP, J = idx % PP;
     const int c = c0 + cl;
@@ -874,22 +860,28 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
   }
   __syncthreads();
 
+  const int WL = g.W + Q - 1;
   for (int lagg = 0; lagg < Q; ++lagg) {
     const int NU = TC + Q - 1 - lagg;
-    const int KW = NU + 2 * g.Ra;
-    vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
-    __syncthreads();
-    const int nch = (NU + kRunChunk - 1) / kRunChunk;
-    for (int idx = threadIdx.x; idx < PP * nch; idx += blockDim.x) {
-      const int ch = idx % nch, J = idx / nch;
-      float4* out = lag + J * NUmax;
-      ring_sums_run(Vo + J * KW, Vg + J * KW, g, ch * kRunChunk, min(NU, (ch + 1) * kRunChunk),
-                    [&](int u, longlong2 L) {
-                      float4 v;
-                      ll_to_ff(L.x, v.x, v.y);
-                      ll_to_ff(L.y, v.z, v.w);
-                      out[u] = v;
-                    });
+    if (FROM_STORE) {
+      const float4* src = Lw + ((size_t)r * Q + lagg) * PP * WL;
+      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
+        const int u = idx % NU, J = idx / NU;
+        lag[J * NUmax + u] =
+            (c0 + u < WL) ? __ldg(src + (size_t)J * WL + c0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      const int KW = NU + 2 * g.Ra;
+      vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
+        const int u = idx % NU, J = idx / NU;
+        const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
+        float4 v;
+        ll_to_ff(L.x, v.x, v.y);
+        ll_to_ff(L.y, v.z, v.w);
+        lag[J * NUmax + u] = v;
+      }
     }
     __syncthreads();
     // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float
