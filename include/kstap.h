@@ -151,6 +151,63 @@ enum {
 kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable);
 kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launches, int n);
 
+/* ------------------------------------------------------------ batches ----
+ * One frame of a batch: the frame Y (device, p x H_in x W_in complex64), its
+ * caller-owned factor arrays and outputs (device, H * W cells; layouts as in
+ * kstap_factors / kstap_detect; T_all may be NULL). */
+typedef struct {
+  const kstap_c64* Y;
+  int H_in, W_in;
+  kstap_factors factors;
+  float* Tmax;
+  int32_t* vidx;
+  uint8_t* map;
+  float* T_all;
+} kstap_frame;
+
+/* Batched fit + detect of n frames of different sizes that share the
+ * context's parameters and bank.  Every kernel of the path is launched once
+ * for the whole batch (persistent grids over the tiles of all frames), so
+ * many small tiles cost five launches, not five per tile.  The workspace
+ * grows to the batch's needs (KSTAP_ENOMEM over budget); the device job table
+ * is uploaded on the context stream.  Results are identical to per-frame
+ * kstap_fit_project + kstap_detect calls (same kernels, same tiling of each
+ * frame). */
+kstap_status kstap_run_batch(kstap_ctx* ctx, const kstap_frame* frames, int n);
+
+/* A CUDA graph over batches of several contexts (e.g. one per (q, r_b)
+ * class of a mixed batch): ctxs[c] processes frames[c][0 .. nframes[c]-1].
+ * The graph owns its own workspaces and job tables (allocated here, outside
+ * the capture), captures each context's batch on its own branch stream
+ * (fork / join), and is instantiated once; kstap_graph_launch replays it on
+ * cuda_stream (a cudaStream_t).  Frame pointers and sizes are baked in: to
+ * process new data, write it into the same device buffers and relaunch.  The
+ * contexts must outlive the graph.  Errors: kstap_last_error(NULL). */
+typedef struct kstap_graph kstap_graph;
+kstap_status kstap_graph_create(kstap_ctx* const* ctxs, const kstap_frame* const* frames,
+                                const int* nframes, int nctx, kstap_graph** out);
+kstap_status kstap_graph_launch(kstap_graph* graph, void* cuda_stream);
+kstap_status kstap_graph_destroy(kstap_graph* graph);
+
+/* Launch tuning of a context.  waves: persistent grid size in multiples of
+ * (SMs x resident CTAs), 1..64; tc: cells per tile of the B / U_B pass
+ * (0 = default: 32, or 16 at q = 32; allowed 8, 16, 32 with tc = 32 only for
+ * q <= 16).  Tuning changes only the schedule, not the arithmetic of any
+ * cell. */
+typedef struct {
+  int waves;
+  int tc;
+  float ms_per_batch; /* measured by kstap_autotune */
+} kstap_tuning;
+
+/* Autotuner: times kstap_run_batch on these frames (reps repetitions after a
+ * warm-up) for every candidate (waves in {1,2,4,8,16}) x (tc in {16,32}, or
+ * {8,16} at q = 32), keeps the fastest in the context and reports it.
+ * Synchronises the context stream. */
+kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, int reps,
+                            kstap_tuning* out);
+kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* tuning);
+
 /* Allocation-free variant of kstap_fit_project.  The paper has no
  * counterpart: this exists for callers that must not allocate device memory
  * while they run -- for example a real-time processing loop, where cudaMalloc

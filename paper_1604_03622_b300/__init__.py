@@ -20,7 +20,9 @@ STATUS = {0: "KSTAP_OK", -1: "KSTAP_EINVAL", -2: "KSTAP_ENOMEM", -3: "KSTAP_ECUD
 
 EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
             "kstap_last_error", "kstap_workspace_bytes", "kstap_set_profiling",
-            "kstap_kernel_times", "kstap_fit_project_noalloc"]
+            "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
+            "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
+            "kstap_set_tuning"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -35,6 +37,16 @@ class KstapFactors(ctypes.Structure):
     _fields_ = [("UA", ctypes.c_void_p), ("UB_hi", ctypes.c_void_p), ("UB_lo", ctypes.c_void_p),
                 ("lamA", ctypes.c_void_p), ("lamB", ctypes.c_void_p), ("iters", ctypes.c_void_p),
                 ("eta", ctypes.c_void_p)]
+
+
+class KstapFrame(ctypes.Structure):
+    _fields_ = [("Y", ctypes.c_void_p), ("H_in", ctypes.c_int), ("W_in", ctypes.c_int),
+                ("factors", KstapFactors), ("Tmax", ctypes.c_void_p), ("vidx", ctypes.c_void_p),
+                ("map", ctypes.c_void_p), ("T_all", ctypes.c_void_p)]
+
+
+class KstapTuning(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_int), ("tc", ctypes.c_int), ("ms_per_batch", ctypes.c_float)]
 
 
 class KstapError(RuntimeError):
@@ -64,10 +76,22 @@ def lib() -> ctypes.CDLL:
         L.kstap_workspace_bytes.restype = Z
         L.kstap_fit_project_noalloc.argtypes = [ctypes.POINTER(KstapParams), P, I, I,
                                                 ctypes.POINTER(KstapFactors), P]
+        L.kstap_run_batch.argtypes = [P, ctypes.POINTER(KstapFrame), I]
+        L.kstap_graph_create.argtypes = [ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.POINTER(KstapFrame)),
+                                         ctypes.POINTER(ctypes.c_int), I,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        L.kstap_graph_launch.argtypes = [P, P]
+        L.kstap_graph_destroy.argtypes = [P]
+        L.kstap_autotune.argtypes = [P, ctypes.POINTER(KstapFrame), I, I,
+                                     ctypes.POINTER(KstapTuning)]
+        L.kstap_set_tuning.argtypes = [P, ctypes.POINTER(KstapTuning)]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
         for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
-                     "kstap_set_profiling", "kstap_kernel_times", "kstap_fit_project_noalloc"):
+                     "kstap_set_profiling", "kstap_kernel_times", "kstap_fit_project_noalloc",
+                     "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
+                     "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -143,3 +167,47 @@ def kstap_fit_project_noalloc(params: KstapParams, Y, H_in: int, W_in: int,
     """Allocation-free fit (no context, static device scratch, <= 32768 cells)."""
     _check(lib().kstap_fit_project_noalloc(ctypes.byref(params), _ptr(Y), H_in, W_in,
                                            ctypes.byref(factors), stream or None))
+
+
+def make_frame(Y, H_in: int, W_in: int, factors: KstapFactors, Tmax, vidx, map_,
+               T_all=None) -> KstapFrame:
+    return KstapFrame(_ptr(Y), H_in, W_in, factors, _ptr(Tmax), _ptr(vidx), _ptr(map_),
+                      _ptr(T_all))
+
+
+def kstap_run_batch(ctx: int, frames) -> None:
+    arr = (KstapFrame * len(frames))(*frames)
+    _check(lib().kstap_run_batch(ctx, arr, len(frames)), ctx)
+
+
+def kstap_graph_create(ctxs, frames_per_ctx) -> int:
+    """One CUDA graph over several contexts' batches (frames_per_ctx[c] for ctxs[c])."""
+    n = len(ctxs)
+    arrays = [(KstapFrame * len(f))(*f) for f in frames_per_ctx]
+    fptrs = (ctypes.POINTER(KstapFrame) * n)(*[ctypes.cast(a, ctypes.POINTER(KstapFrame))
+                                                for a in arrays])
+    counts = (ctypes.c_int * n)(*[len(f) for f in frames_per_ctx])
+    cptrs = (ctypes.c_void_p * n)(*ctxs)
+    out = ctypes.c_void_p()
+    _check(lib().kstap_graph_create(cptrs, fptrs, counts, n, ctypes.byref(out)))
+    return out.value
+
+
+def kstap_graph_launch(graph: int, stream: int = 0) -> None:
+    _check(lib().kstap_graph_launch(graph, stream or None))
+
+
+def kstap_graph_destroy(graph: int) -> None:
+    _check(lib().kstap_graph_destroy(graph))
+
+
+def kstap_autotune(ctx: int, frames, reps: int = 3) -> KstapTuning:
+    arr = (KstapFrame * len(frames))(*frames)
+    t = KstapTuning()
+    _check(lib().kstap_autotune(ctx, arr, len(frames), reps, ctypes.byref(t)), ctx)
+    return t
+
+
+def kstap_set_tuning(ctx: int, waves: int, tc: int = 0) -> None:
+    t = KstapTuning(waves, tc, 0.0)
+    _check(lib().kstap_set_tuning(ctx, ctypes.byref(t)), ctx)

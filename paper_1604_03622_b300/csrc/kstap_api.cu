@@ -1,11 +1,17 @@
 // libkstap: C ABI (include/kstap.h) over the Kron-STAP kernels.
+//
+// Every launch works on a job list: one frame passed by value (the per-frame
+// calls) or a device table of frames (batches and CUDA graphs).  Kernels use
+// persistent grids (occupancy x waves CTAs striding over all tiles of all
+// jobs of the launch).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
-#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -13,6 +19,15 @@
 #include "kstap_kernels.cuh"
 
 using kstap::Geom;
+using kstap::Job;
+using kstap::JobList;
+
+namespace {
+struct Tuning {
+  int waves = 4;   // persistent grid = SMs x resident CTAs x waves (capped by tiles)
+  int tc = 0;      // cells per tile in the B pass (0 = default: 32, or 16 for q = 32)
+};
+}  // namespace
 
 struct kstap_ctx {
   kstap_params prm;
@@ -20,13 +35,17 @@ struct kstap_ctx {
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   int device = 0;
+  int sm_count = 148;
   // bank, transposed for the detect kernel: aT [p][V], bT [q][V], norms [2V]
   float2* bank_aT = nullptr;
   float2* bank_bT = nullptr;
   float* bank_n2 = nullptr;
-  // workspace
+  // workspace and the device job table of kstap_run_batch
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  Job* jobs_dev = nullptr;
+  size_t jobs_cap = 0;
+  Tuning tune;
   std::string err;
   // optional per-kernel timing: events around every launch on ctx->stream
   bool profile = false;
@@ -36,32 +55,36 @@ struct kstap_ctx {
   bool ev_pending[kstap_nkernels] = {};
 };
 
+struct kstap_graph {
+  std::vector<void*> allocs;          // workspaces and job tables owned by the graph
+  std::vector<cudaStream_t> streams;  // capture root and branches
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 thread_local std::string g_create_err;
 
-// Records the start event of kernel `k` (profiling mode only).
-void prof_begin(kstap_ctx* ctx, int k) {
-  if (!ctx->profile) return;
+void prof_begin(kstap_ctx* ctx, int k, cudaStream_t s) {
+  if (!ctx || !ctx->profile) return;
   if (!ctx->ev[k][0]) {
     cudaEventCreate(&ctx->ev[k][0]);
     cudaEventCreate(&ctx->ev[k][1]);
   }
-  cudaEventRecord(ctx->ev[k][0], ctx->stream);
+  cudaEventRecord(ctx->ev[k][0], s);
 }
 
-// Records the end event of kernel `k`; the elapsed time is collected lazily.
-void prof_end(kstap_ctx* ctx, int k) {
-  if (!ctx->profile) return;
-  cudaEventRecord(ctx->ev[k][1], ctx->stream);
+void prof_end(kstap_ctx* ctx, int k, cudaStream_t s) {
+  if (!ctx || !ctx->profile) return;
+  cudaEventRecord(ctx->ev[k][1], s);
   ctx->ev_pending[k] = true;
 }
 
-// Folds finished launches into the per-kernel totals (synchronises on each
-// pending end event; called before the next launch of the same kernel and by
-// kstap_kernel_times).
+// Folds a finished launch into the per-kernel totals (waits for its end event;
+// called before the next launch of the same kernel and by kstap_kernel_times).
 void prof_collect(kstap_ctx* ctx, int k) {
-  if (!ctx->ev_pending[k]) return;
+  if (!ctx || !ctx->ev_pending[k]) return;
   cudaEventSynchronize(ctx->ev[k][1]);
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, ctx->ev[k][0], ctx->ev[k][1]) == cudaSuccess) {
@@ -140,8 +163,8 @@ bool valid_params(const kstap_params* p, std::string& why) {
   return true;
 }
 
-Geom make_geom(const kstap_ctx* ctx, int H_in, int W_in) {
-  const kstap_params& p = ctx->prm;
+// Class-wide geometry (per-frame sizes are filled per tile from the job).
+Geom make_geom(const kstap_params& p, int V, int tc) {
   Geom g;
   g.p = p.p;
   g.q = p.q;
@@ -151,13 +174,10 @@ Geom make_geom(const kstap_ctx* ctx, int H_in, int W_in) {
   g.Ra = p.ring_a;
   g.Gr = p.guard_r;
   g.Ga = p.guard_a;
-  g.H_in = H_in;
-  g.W_in = W_in;
-  g.H = H_in - 2 * p.ring_r;
-  g.W = W_in - 2 * p.ring_a - p.q + 1;
+  g.H_in = g.W_in = g.H = g.W = 0;
   const long nbox = (2L * p.ring_r + 1) * (2L * p.ring_a + 1);
   g.n = (int)(nbox - (2L * p.guard_r + 1) * (2L * p.guard_a + 1));
-  g.V = ctx->V;
+  g.V = V;
   // |Y| < 2^B per component keeps every box sum of products below 2^62:
   // 2B + 1 + ceil(log2(nbox)) <= 62.
   g.B = (61 - ceil_log2(nbox)) / 2;
@@ -165,26 +185,108 @@ Geom make_geom(const kstap_ctx* ctx, int H_in, int W_in) {
   g.max_iter = p.max_iter > 0 ? p.max_iter : 64;
   g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
   g.tau = p.tau;
-  g.tc = (p.q >= 32) ? 16 : kstap::kTileCells;
+  g.tc = tc > 0 ? tc : ((p.q >= 32) ? 16 : kstap::kTileCells);
   return g;
 }
 
-// workspace layout (struct of arrays per cell, plus the optional lag store)
-struct WsLayout {
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch layout of one launch over frames with cell grids H x W: per-job
+// scale words, per-cell arrays (struct of arrays over all cells of all
+// jobs), then the per-job lag stores.
+struct Layout {
   size_t flags, Mw, Sw, aw, Lw, total;
+  size_t NC;
+  std::vector<size_t> cell0, lag0;   // per job (lag0 in float4 units)
 };
 
-WsLayout ws_layout(int p, int q, size_t H, size_t W, bool lag_store) {
-  const size_t PP = (size_t)p * p, NE = PP * (PP + 1) / 2, ncell = H * W;
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  WsLayout L;
+Layout make_layout(const kstap_params& p, const std::vector<std::pair<int, int>>& HW,
+                   bool lag_store) {
+  const size_t PP = (size_t)p.p * p.p, NE = PP * (PP + 1) / 2;
+  Layout L;
+  L.NC = 0;
+  size_t lag = 0;
+  for (auto& hw : HW) {
+    L.cell0.push_back(L.NC);
+    L.lag0.push_back(lag);
+    L.NC += (size_t)hw.first * hw.second;
+    if (lag_store) lag += (size_t)hw.first * p.q * PP * (hw.second + p.q - 1);
+  }
   L.flags = 0;
-  L.Mw = 256;
-  L.Sw = up(L.Mw + ncell * NE * sizeof(float2));
-  L.aw = up(L.Sw + ncell * PP * sizeof(float2));
-  L.Lw = up(L.aw + ncell * PP * sizeof(float2));
-  L.total = L.Lw + (lag_store ? up(H * q * PP * (W + q - 1) * sizeof(float4)) : 0);
+  L.Mw = up256(8 * HW.size());
+  L.Sw = up256(L.Mw + L.NC * NE * sizeof(float2));
+  L.aw = up256(L.Sw + L.NC * PP * sizeof(float2));
+  L.Lw = up256(L.aw + L.NC * PP * sizeof(float2));
+  L.total = up256(L.Lw + lag * sizeof(float4));
   return L;
+}
+
+int tiles_moments(int H, int W) {
+  return ((W + kstap::kTileCells - 1) / kstap::kTileCells) *
+         ((H + kstap::kMomRows - 1) / kstap::kMomRows);
+}
+int tiles_flip(int H, int W) { return (int)(((size_t)H * W + 127) / 128); }
+int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
+int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
+int tiles_detect(int H, int W, int q) {
+  const int c = cells_per_detect_block(q);
+  return (int)(((size_t)H * W + c - 1) / c);
+}
+
+// A frame as the library sees it (device pointers, caller-owned).
+struct Frame {
+  const kstap_c64* Y;
+  int H_in, W_in;
+  kstap_factors f;
+  float* Tmax;
+  int32_t* vidx;
+  uint8_t* map;
+  float* T_all;
+};
+
+// Fills the jobs of one launch; scratch and L may be null (detect-only).
+void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& fr, char* scratch,
+               const Layout* L, std::vector<Job>& jobs, JobList& JL) {
+  jobs.clear();
+  int t[4] = {0, 0, 0, 0};
+  for (size_t k = 0; k < fr.size(); ++k) {
+    Job j;
+    memset(&j, 0, sizeof(j));
+    j.Y = (const float2*)fr[k].Y;
+    j.H_in = fr[k].H_in;
+    j.W_in = fr[k].W_in;
+    j.H = fr[k].H_in - 2 * p.ring_r;
+    j.W = fr[k].W_in - 2 * p.ring_a - p.q + 1;
+    j.cell0 = L ? (long long)L->cell0[k] : 0;
+    j.lag0 = L ? (long long)L->lag0[k] : 0;
+    j.maxbits = (scratch && L) ? (unsigned*)(scratch + L->flags) + 2 * k : nullptr;
+    j.UA = (float2*)fr[k].f.UA;
+    j.UBh = (float2*)fr[k].f.UB_hi;
+    j.UBl = (float2*)fr[k].f.UB_lo;
+    j.lamA = fr[k].f.lamA;
+    j.lamB = fr[k].f.lamB;
+    j.iters = fr[k].f.iters;
+    j.eta = fr[k].f.eta;
+    j.Tmax = fr[k].Tmax;
+    j.vidx = fr[k].vidx;
+    j.map = fr[k].map;
+    j.T_all = fr[k].T_all;
+    j.tile0[kstap::kKindMoments] = t[0];
+    j.tile0[kstap::kKindFlip] = t[1];
+    j.tile0[kstap::kKindBfit] = t[2];
+    j.tile0[kstap::kKindDetect] = t[3];
+    t[0] += tiles_moments(j.H, j.W);
+    t[1] += tiles_flip(j.H, j.W);
+    t[2] += tiles_bfit(j.H, j.W, g.tc);
+    t[3] += tiles_detect(j.H, j.W, p.q);
+    jobs.push_back(j);
+  }
+  memset(&JL, 0, sizeof(JL));
+  if (!jobs.empty()) JL.one = jobs[0];
+  JL.table = nullptr;
+  JL.njobs = (int)jobs.size();
+  for (int k = 0; k < 4; ++k) JL.ntiles[k] = t[k];
+  JL.NC = L ? (long long)L->NC : 0;
 }
 
 size_t smem_moments(const Geom& g) {
@@ -213,89 +315,116 @@ size_t smem_bfit(const Geom& g, bool from_store) {
 size_t smem_detect(const Geom& g) {
   const int P = g.p, Q = g.q, V = g.V, R = g.r_b;
   const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 2 * (size_t)P * R;
-  const size_t cells = (kstap::kThreads / 32) * (32 / Q);
+  const size_t cells = cells_per_detect_block(Q);
   return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8;
 }
 
-// Enqueues the fit (scale, moments, flip-flop, B / U_B) on stream s with the
-// given scratch; ctx (may be NULL) receives errors and profiling events.
+// Persistent grid: SMs x resident CTAs x waves, capped by the tile count.
+template <typename K>
+int grid_for(K kernel, int threads, size_t smem, int tiles, int sm_count, int waves) {
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const long cap = (long)sm_count * occ * std::max(1, waves);
+  return (int)std::max(1L, std::min<long>(tiles, cap));
+}
+
+// Enqueues the fit (scale, moments, flip-flop, B / U_B) of all jobs of JL.
 template <int P, int Q, int R>
-kstap_status enqueue_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
-                         const WsLayout& L, bool lag_store, const kstap_factors* f,
+kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                         char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
                          cudaStream_t s) {
-  unsigned* maxbits = (unsigned*)(scratch + L.flags);
-  float4* Lw = lag_store ? (float4*)(scratch + L.Lw) : nullptr;
   float2* Mw = (float2*)(scratch + L.Mw);
   float2* Sw = (float2*)(scratch + L.Sw);
   float2* aw = (float2*)(scratch + L.aw);
-  const size_t ncell = (size_t)g.H * g.W;
-  KSTAP_CUDA(ctx, cudaMemsetAsync(maxbits, 0, 8, s));   // the scale words must start at zero
-  const size_t nfloat = 2 * (size_t)g.p * g.H_in * g.W_in;
-  int blocks = (int)std::min<size_t>((nfloat + 1023) / 1024, 148 * 16);
-  if (blocks < 1) blocks = 1;
-  if (ctx) prof_collect(ctx, KSTAP_K_SCALE), prof_begin(ctx, KSTAP_K_SCALE);
-  kstap::k_frame_maxabs<<<blocks, 256, 0, s>>>((const float*)Y, nfloat, maxbits, maxbits + 1);
-  if (ctx) prof_end(ctx, KSTAP_K_SCALE);
+  float4* Lw = lag_store ? (float4*)(scratch + L.Lw) : nullptr;
+  if (JL.njobs < 1) return KSTAP_OK;
+  KSTAP_CUDA(ctx, cudaMemsetAsync(scratch + L.flags, 0, 8 * (size_t)JL.njobs, s));
+  const size_t maxf = JL.table ? 0 : 2 * (size_t)P * JL.one.H_in * JL.one.W_in;
+  const int bx = JL.table ? sm_count * 2
+                          : (int)std::min<size_t>((maxf + 1023) / 1024, (size_t)sm_count * 16);
+  prof_collect(prof, KSTAP_K_SCALE);
+  prof_begin(prof, KSTAP_K_SCALE, s);
+  kstap::k_frame_maxabs<<<dim3(std::max(1, bx), JL.njobs), 256, 0, s>>>(g, JL);
+  prof_end(prof, KSTAP_K_SCALE, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
   const size_t sm1 = smem_moments(g);
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_moments<P, Q>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-  dim3 grid1((g.W + kstap::kTileCells - 1) / kstap::kTileCells,
-             (g.H + kstap::kMomRows - 1) / kstap::kMomRows);
-  if (ctx) prof_collect(ctx, KSTAP_K_MOMENTS), prof_begin(ctx, KSTAP_K_MOMENTS);
-  kstap::k_moments<P, Q><<<grid1, kstap::kMomThreads, sm1, s>>>(Y, g, maxbits, Mw, Sw, Lw);
-  if (ctx) prof_end(ctx, KSTAP_K_MOMENTS);
+  const int g1 = grid_for(kstap::k_moments<P, Q>, kstap::kMomThreads, sm1,
+                          JL.ntiles[kstap::kKindMoments], sm_count, waves);
+  prof_collect(prof, KSTAP_K_MOMENTS);
+  prof_begin(prof, KSTAP_K_MOMENTS, s);
+  kstap::k_moments<P, Q><<<g1, kstap::kMomThreads, sm1, s>>>(g, JL, Mw, Sw, Lw);
+  prof_end(prof, KSTAP_K_MOMENTS, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
-  if (ctx) prof_collect(ctx, KSTAP_K_FLIPFLOP), prof_begin(ctx, KSTAP_K_FLIPFLOP);
-  kstap::k_flipflop<P><<<(unsigned)((ncell + 127) / 128), 128, 0, s>>>(
-      Mw, Sw, g, ncell, aw, (float2*)f->UA, f->lamA, f->iters, f->eta);
-  if (ctx) prof_end(ctx, KSTAP_K_FLIPFLOP);
+  const int g2 = grid_for(kstap::k_flipflop<P>, 128, 0, JL.ntiles[kstap::kKindFlip], sm_count,
+                          waves);
+  prof_collect(prof, KSTAP_K_FLIPFLOP);
+  prof_begin(prof, KSTAP_K_FLIPFLOP, s);
+  kstap::k_flipflop<P><<<g2, 128, 0, s>>>(g, JL, Mw, Sw, aw);
+  prof_end(prof, KSTAP_K_FLIPFLOP, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
   const size_t sm3 = smem_bfit(g, lag_store);
   auto kb = lag_store ? kstap::k_bfit<P, Q, R, true> : kstap::k_bfit<P, Q, R, false>;
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-  dim3 grid3((g.W + g.tc - 1) / g.tc, g.H);
-  if (ctx) prof_collect(ctx, KSTAP_K_BFIT), prof_begin(ctx, KSTAP_K_BFIT);
-  kb<<<grid3, kstap::kThreads, sm3, s>>>(Y, g, maxbits, aw, Lw, (float2*)f->UB_hi,
-                                          (float2*)f->UB_lo, f->lamB);
-  if (ctx) prof_end(ctx, KSTAP_K_BFIT);
+  const int g3 = grid_for(kb, kstap::kThreads, sm3, JL.ntiles[kstap::kKindBfit], sm_count, waves);
+  prof_collect(prof, KSTAP_K_BFIT);
+  prof_begin(prof, KSTAP_K_BFIT, s);
+  kb<<<g3, kstap::kThreads, sm3, s>>>(g, JL, aw, Lw);
+  prof_end(prof, KSTAP_K_BFIT, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;
-}
-
-kstap_status dispatch_fit(kstap_ctx* ctx, const Geom& g, const float2* Y, char* scratch,
-                          const WsLayout& L, bool lag_store, const kstap_factors* f,
-                          cudaStream_t s) {
-#define KSTAP_FIT(QQ, RR)        \
-  if (g.q == QQ && g.r_b == RR) \
-    return enqueue_fit<3, QQ, RR>(ctx, g, Y, scratch, L, lag_store, f, s);
-  KSTAP_FIT(8, 1) KSTAP_FIT(8, 2) KSTAP_FIT(8, 3) KSTAP_FIT(8, 4)
-  KSTAP_FIT(16, 1) KSTAP_FIT(16, 2) KSTAP_FIT(16, 3) KSTAP_FIT(16, 4)
-  KSTAP_FIT(32, 1) KSTAP_FIT(32, 2) KSTAP_FIT(32, 3) KSTAP_FIT(32, 4)
-#undef KSTAP_FIT
-  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
 }
 
 template <int P, int Q, int R>
-kstap_status launch_detect(kstap_ctx* ctx, const Geom& g, const float2* Y, const kstap_factors* f,
-                           float* Tmax, int32_t* vidx, uint8_t* map, float* T_all) {
-  const size_t ncell = (size_t)g.H * g.W;
+kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                            int sm_count, int waves, cudaStream_t s) {
+  if (JL.njobs < 1) return KSTAP_OK;
   const size_t sm = smem_detect(g);
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const size_t per_block = (kstap::kThreads / 32) * (32 / Q);
-  const unsigned grid = (unsigned)((ncell + per_block - 1) / per_block);
-  prof_collect(ctx, KSTAP_K_DETECT);
-  prof_begin(ctx, KSTAP_K_DETECT);
-  kstap::k_detect<P, Q, R><<<grid, kstap::kThreads, sm, ctx->stream>>>(
-      Y, g, ctx->bank_aT, ctx->bank_bT, ctx->bank_n2, (const float2*)f->UA,
-      (const float2*)f->UB_hi, (const float2*)f->UB_lo, Tmax, vidx, map, T_all);
-  prof_end(ctx, KSTAP_K_DETECT);
+  const int grid = grid_for(kstap::k_detect<P, Q, R>, kstap::kThreads, sm,
+                            JL.ntiles[kstap::kKindDetect], sm_count, waves);
+  prof_collect(prof, KSTAP_K_DETECT);
+  prof_begin(prof, KSTAP_K_DETECT, s);
+  kstap::k_detect<P, Q, R><<<grid, kstap::kThreads, sm, s>>>(g, JL, ctx->bank_aT, ctx->bank_bT,
+                                                               ctx->bank_n2);
+  prof_end(prof, KSTAP_K_DETECT, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;
+}
+
+#define KSTAP_DISPATCH(QQ, RR, CALL) \
+  if (g.q == QQ && g.r_b == RR) return CALL;
+#define KSTAP_DISPATCH_ALL(CALLT)                                         \
+  KSTAP_DISPATCH(8, 1, CALLT(8, 1)) KSTAP_DISPATCH(8, 2, CALLT(8, 2))     \
+  KSTAP_DISPATCH(8, 3, CALLT(8, 3)) KSTAP_DISPATCH(8, 4, CALLT(8, 4))     \
+  KSTAP_DISPATCH(16, 1, CALLT(16, 1)) KSTAP_DISPATCH(16, 2, CALLT(16, 2)) \
+  KSTAP_DISPATCH(16, 3, CALLT(16, 3)) KSTAP_DISPATCH(16, 4, CALLT(16, 4)) \
+  KSTAP_DISPATCH(32, 1, CALLT(32, 1)) KSTAP_DISPATCH(32, 2, CALLT(32, 2)) \
+  KSTAP_DISPATCH(32, 3, CALLT(32, 3)) KSTAP_DISPATCH(32, 4, CALLT(32, 4))
+
+kstap_status dispatch_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                          char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
+                          cudaStream_t s) {
+#define KSTAP_FITC(QQ, RR) \
+  enqueue_fit<3, QQ, RR>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s)
+  KSTAP_DISPATCH_ALL(KSTAP_FITC)
+#undef KSTAP_FITC
+  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
+}
+
+kstap_status dispatch_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                             int sm_count, int waves, cudaStream_t s) {
+#define KSTAP_DETC(QQ, RR) enqueue_detect<3, QQ, RR>(ctx, prof, g, JL, sm_count, waves, s)
+  KSTAP_DISPATCH_ALL(KSTAP_DETC)
+#undef KSTAP_DETC
+  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
 }
 
 kstap_status check_frame(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in) {
@@ -310,6 +439,69 @@ kstap_status check_frame(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in)
   return KSTAP_OK;
 }
 
+kstap_status check_factors(kstap_ctx* ctx, const kstap_factors* f) {
+  if (!f || !f->UA || !f->UB_hi || !f->UB_lo)
+    return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
+  return KSTAP_OK;
+}
+
+// Grows ctx->ws to `bytes` within the budget (synchronises the stream when
+// replacing a smaller workspace).
+kstap_status ensure_ws(kstap_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return KSTAP_OK;
+  if (ctx->budget && bytes > ctx->budget)
+    return fail(ctx, KSTAP_ENOMEM, "workspace %zu B exceeds the HBM budget %zu B", bytes,
+                ctx->budget);
+  if (ctx->ws) {
+    KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess)
+    return fail(ctx, KSTAP_ENOMEM, "workspace cudaMalloc(%zu) failed: %s", bytes,
+                cudaGetErrorString(e));
+  ctx->ws_bytes = bytes;
+  return KSTAP_OK;
+}
+
+kstap_status frames_from(kstap_ctx* ctx, const kstap_frame* frames, int n,
+                         std::vector<Frame>& fr, std::vector<std::pair<int, int>>& HW) {
+  if (n < 1 || !frames) return fail(ctx, KSTAP_EINVAL, "need at least one frame");
+  fr.clear();
+  HW.clear();
+  const kstap_params& p = ctx->prm;
+  for (int k = 0; k < n; ++k) {
+    kstap_status st = check_frame(ctx, frames[k].Y, frames[k].H_in, frames[k].W_in);
+    if (st != KSTAP_OK) return st;
+    st = check_factors(ctx, &frames[k].factors);
+    if (st != KSTAP_OK) return st;
+    if (!frames[k].Tmax || !frames[k].vidx || !frames[k].map)
+      return fail(ctx, KSTAP_EINVAL, "frame %d: Tmax, vidx and map are required", k);
+    fr.push_back(Frame{frames[k].Y, frames[k].H_in, frames[k].W_in, frames[k].factors,
+                       frames[k].Tmax, frames[k].vidx, frames[k].map, frames[k].T_all});
+    HW.push_back({frames[k].H_in - 2 * p.ring_r, frames[k].W_in - 2 * p.ring_a - p.q + 1});
+  }
+  return KSTAP_OK;
+}
+
+// Enqueues fit + detect of all frames on stream s with the given scratch and
+// device job table (unused for a single frame, whose job goes by value).
+kstap_status enqueue_batch(kstap_ctx* ctx, kstap_ctx* prof, const std::vector<Frame>& fr,
+                           const Layout& L, char* scratch, const Job* jobs_dev,
+                           cudaStream_t s) {
+  const Geom g = make_geom(ctx->prm, ctx->V, ctx->tune.tc);
+  std::vector<Job> host;
+  JobList JL;
+  fill_jobs(ctx->prm, g, fr, scratch, &L, host, JL);
+  if (fr.size() > 1) JL.table = jobs_dev;
+  kstap_status st = dispatch_fit(ctx, prof, g, JL, scratch, L, true, ctx->sm_count,
+                                 ctx->tune.waves, s);
+  if (st != KSTAP_OK) return st;
+  return dispatch_detect(ctx, prof, g, JL, ctx->sm_count, ctx->tune.waves, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -320,7 +512,7 @@ size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in) {
   const long H = H_in - 2L * params->ring_r;
   const long W = W_in - 2L * params->ring_a - params->q + 1;
   if (H < 1 || W < 1) return 0;
-  return ws_layout(params->p, params->q, (size_t)H, (size_t)W, true).total;
+  return make_layout(*params, {{(int)H, (int)W}}, true).total;
 }
 
 kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
@@ -338,6 +530,8 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->budget = hbm_budget_bytes;
   cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->sm_count < 1) ctx->sm_count = 148;
   const int p = params->p, q = params->q;
   std::vector<kstap_c64> ha((size_t)V * p), hb((size_t)V * q);
   cudaError_t e = cudaMemcpy(ha.data(), bank_a, ha.size() * sizeof(kstap_c64), cudaMemcpyDefault);
@@ -385,28 +579,20 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
                                const kstap_factors* factors) {
   kstap_status st = check_frame(ctx, Y, H_in, W_in);
   if (st != KSTAP_OK) return st;
-  if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
-    return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
-  const Geom g = make_geom(ctx, H_in, W_in);
-  const size_t ncell = (size_t)g.H * g.W;
-  const WsLayout L = ws_layout(g.p, g.q, g.H, g.W, true);
-  if (L.total > ctx->ws_bytes) {
-    if (ctx->budget && L.total > ctx->budget)
-      return fail(ctx, KSTAP_ENOMEM, "workspace %zu B exceeds the HBM budget %zu B", L.total,
-                  ctx->budget);
-    if (ctx->ws) {
-      KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      cudaFree(ctx->ws);
-      ctx->ws = nullptr;
-      ctx->ws_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&ctx->ws, L.total);
-    if (e != cudaSuccess)
-      return fail(ctx, KSTAP_ENOMEM, "workspace cudaMalloc(%zu) failed: %s", L.total,
-                  cudaGetErrorString(e));
-    ctx->ws_bytes = L.total;
-  }
-  return dispatch_fit(ctx, g, (const float2*)Y, (char*)ctx->ws, L, true, factors, ctx->stream);
+  st = check_factors(ctx, factors);
+  if (st != KSTAP_OK) return st;
+  const kstap_params& p = ctx->prm;
+  const int H = H_in - 2 * p.ring_r, W = W_in - 2 * p.ring_a - p.q + 1;
+  const Layout L = make_layout(p, {{H, W}}, true);
+  st = ensure_ws(ctx, L.total);
+  if (st != KSTAP_OK) return st;
+  const Geom g = make_geom(p, ctx->V, ctx->tune.tc);
+  std::vector<Frame> fr{Frame{Y, H_in, W_in, *factors, nullptr, nullptr, nullptr, nullptr}};
+  std::vector<Job> jobs;
+  JobList JL;
+  fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
+  return dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
+                      ctx->stream);
 }
 
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
@@ -414,19 +600,220 @@ kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
                           float* T_all) {
   kstap_status st = check_frame(ctx, Y, H_in, W_in);
   if (st != KSTAP_OK) return st;
-  if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
-    return fail(ctx, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
+  st = check_factors(ctx, factors);
+  if (st != KSTAP_OK) return st;
   if (!Tmax || !vidx || !map) return fail(ctx, KSTAP_EINVAL, "Tmax, vidx and map are required");
-  const Geom g = make_geom(ctx, H_in, W_in);
-  const float2* Yf = (const float2*)Y;
-#define KSTAP_DET(QQ, RR)                                                                 \
-  if (g.q == QQ && g.r_b == RR) return launch_detect<3, QQ, RR>(ctx, g, Yf, factors, Tmax, vidx, \
-                                                                map, T_all);
-  KSTAP_DET(8, 1) KSTAP_DET(8, 2) KSTAP_DET(8, 3) KSTAP_DET(8, 4)
-  KSTAP_DET(16, 1) KSTAP_DET(16, 2) KSTAP_DET(16, 3) KSTAP_DET(16, 4)
-  KSTAP_DET(32, 1) KSTAP_DET(32, 2) KSTAP_DET(32, 3) KSTAP_DET(32, 4)
-#undef KSTAP_DET
-  return fail(ctx, KSTAP_EINVAL, "unsupported q");
+  const Geom g = make_geom(ctx->prm, ctx->V, ctx->tune.tc);
+  std::vector<Frame> fr{Frame{Y, H_in, W_in, *factors, Tmax, vidx, map, T_all}};
+  std::vector<Job> jobs;
+  JobList JL;
+  fill_jobs(ctx->prm, g, fr, nullptr, nullptr, jobs, JL);
+  return dispatch_detect(ctx, ctx, g, JL, ctx->sm_count, ctx->tune.waves, ctx->stream);
+}
+
+kstap_status kstap_run_batch(kstap_ctx* ctx, const kstap_frame* frames, int n) {
+  if (!ctx) return KSTAP_EINVAL;
+  std::vector<Frame> fr;
+  std::vector<std::pair<int, int>> HW;
+  kstap_status st = frames_from(ctx, frames, n, fr, HW);
+  if (st != KSTAP_OK) return st;
+  const Layout L = make_layout(ctx->prm, HW, true);
+  st = ensure_ws(ctx, L.total);
+  if (st != KSTAP_OK) return st;
+  if (n > 1) {
+    if ((size_t)n > ctx->jobs_cap) {
+      if (ctx->jobs_dev) {
+        KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->jobs_dev);
+        ctx->jobs_dev = nullptr;
+        ctx->jobs_cap = 0;
+      }
+      const size_t cap = std::max<size_t>(n, 64);
+      KSTAP_CUDA(ctx, cudaMalloc(&ctx->jobs_dev, cap * sizeof(Job)));
+      ctx->jobs_cap = cap;
+    }
+    const Geom g = make_geom(ctx->prm, ctx->V, ctx->tune.tc);
+    std::vector<Job> host;
+    JobList JL;
+    fill_jobs(ctx->prm, g, fr, (char*)ctx->ws, &L, host, JL);
+    // stream-ordered upload; pageable source, so the call returns once the
+    // table has been staged and `host` may be released
+    KSTAP_CUDA(ctx, cudaMemcpyAsync(ctx->jobs_dev, host.data(), n * sizeof(Job),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+  }
+  return enqueue_batch(ctx, ctx, fr, L, (char*)ctx->ws, ctx->jobs_dev, ctx->stream);
+}
+
+kstap_status kstap_graph_create(kstap_ctx* const* ctxs, const kstap_frame* const* frames,
+                                const int* nframes, int nctx, kstap_graph** out) {
+  if (!out || !ctxs || !frames || !nframes || nctx < 1)
+    return fail(nullptr, KSTAP_EINVAL, "kstap_graph_create: bad arguments");
+  *out = nullptr;
+  kstap_graph* G = new kstap_graph();
+  auto bail = [&](kstap_status st) {
+    kstap_graph_destroy(G);
+    return st;
+  };
+  struct Plan {
+    std::vector<Frame> fr;
+    Layout L;
+    char* ws = nullptr;
+    Job* jobs = nullptr;
+  };
+  std::vector<Plan> plans(nctx);
+  for (int c = 0; c < nctx; ++c) {
+    kstap_ctx* ctx = ctxs[c];
+    if (!ctx) return bail(fail(nullptr, KSTAP_EINVAL, "context %d is NULL", c));
+    std::vector<std::pair<int, int>> HW;
+    kstap_status st = frames_from(ctx, frames[c], nframes[c], plans[c].fr, HW);
+    if (st != KSTAP_OK) return bail(fail(nullptr, st, "context %d: %s", c, ctx->err.c_str()));
+    plans[c].L = make_layout(ctx->prm, HW, true);
+    void* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, plans[c].L.total);
+    if (e != cudaSuccess)
+      return bail(fail(nullptr, KSTAP_ENOMEM, "graph workspace cudaMalloc(%zu): %s",
+                       plans[c].L.total, cudaGetErrorString(e)));
+    G->allocs.push_back(ws);
+    plans[c].ws = (char*)ws;
+    void* jt = nullptr;
+    e = cudaMalloc(&jt, plans[c].fr.size() * sizeof(Job));
+    if (e != cudaSuccess)
+      return bail(fail(nullptr, KSTAP_ENOMEM, "graph job table: %s", cudaGetErrorString(e)));
+    G->allocs.push_back(jt);
+    plans[c].jobs = (Job*)jt;
+    const Geom g = make_geom(ctx->prm, ctx->V, ctx->tune.tc);
+    std::vector<Job> host;
+    JobList JL;
+    fill_jobs(ctx->prm, g, plans[c].fr, plans[c].ws, &plans[c].L, host, JL);
+    e = cudaMemcpy(jt, host.data(), host.size() * sizeof(Job), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+      return bail(fail(nullptr, KSTAP_ECUDA, "graph job table upload: %s", cudaGetErrorString(e)));
+  }
+  // capture: a root stream forks to one branch per context and joins back
+  for (int c = 0; c <= nctx; ++c) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(nullptr, KSTAP_ECUDA, "cudaStreamCreate failed"));
+    G->streams.push_back(s);
+  }
+  cudaStream_t root = G->streams[0];
+  std::vector<cudaEvent_t> evs(nctx + 1);
+  for (auto& ev : evs) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  kstap_status st = KSTAP_OK;
+  cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecord(evs[0], root);
+    for (int c = 0; c < nctx; ++c) {
+      cudaStream_t s = G->streams[c + 1];
+      cudaStreamWaitEvent(s, evs[0], 0);
+      if (st == KSTAP_OK) {
+        st = enqueue_batch(ctxs[c], nullptr, plans[c].fr, plans[c].L, plans[c].ws, plans[c].jobs,
+                           s);
+        if (st != KSTAP_OK) fail(nullptr, st, "context %d: %s", c, ctxs[c]->err.c_str());
+      }
+      cudaEventRecord(evs[c + 1], s);
+      cudaStreamWaitEvent(root, evs[c + 1], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+    G->graph = graph;
+    if (st == KSTAP_OK && e2 != cudaSuccess)
+      st = fail(nullptr, KSTAP_ECUDA, "stream capture failed: %s", cudaGetErrorString(e2));
+  } else {
+    st = fail(nullptr, KSTAP_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  for (auto& ev : evs) cudaEventDestroy(ev);
+  if (st != KSTAP_OK) return bail(st);
+  e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  if (e != cudaSuccess)
+    return bail(fail(nullptr, KSTAP_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)));
+  *out = G;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_graph_launch(kstap_graph* G, void* cuda_stream) {
+  if (!G || !G->exec) return fail(nullptr, KSTAP_EINVAL, "graph is NULL");
+  cudaError_t e = cudaGraphLaunch(G->exec, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess)
+    return fail(nullptr, KSTAP_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  return KSTAP_OK;
+}
+
+kstap_status kstap_graph_destroy(kstap_graph* G) {
+  if (!G) return KSTAP_EINVAL;
+  if (G->exec) {
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(G->exec);
+  }
+  if (G->graph) cudaGraphDestroy(G->graph);
+  for (auto s : G->streams) cudaStreamDestroy(s);
+  for (auto p : G->allocs) cudaFree(p);
+  delete G;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, int reps,
+                            kstap_tuning* out) {
+  if (!ctx) return KSTAP_EINVAL;
+  if (reps < 1) reps = 3;
+  const Tuning saved = ctx->tune;
+  const bool prof = ctx->profile;
+  ctx->profile = false;
+  const std::vector<int> tcs =
+      (ctx->prm.q >= 32) ? std::vector<int>{8, 16} : std::vector<int>{16, 32};
+  const int wavesv[] = {1, 2, 4, 8, 16};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  Tuning bt = saved;
+  kstap_status st = KSTAP_OK;
+  for (int tc : tcs) {
+    for (int w : wavesv) {
+      ctx->tune.tc = tc;
+      ctx->tune.waves = w;
+      st = kstap_run_batch(ctx, frames, n);   // warm-up (and workspace growth)
+      if (st != KSTAP_OK) break;
+      cudaEventRecord(a, ctx->stream);
+      for (int r = 0; r < reps && st == KSTAP_OK; ++r) st = kstap_run_batch(ctx, frames, n);
+      cudaEventRecord(b, ctx->stream);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= reps;
+      if (st == KSTAP_OK && ms < best) {
+        best = ms;
+        bt = ctx->tune;
+      }
+    }
+    if (st != KSTAP_OK) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->profile = prof;
+  if (st != KSTAP_OK) {
+    ctx->tune = saved;
+    return st;
+  }
+  ctx->tune = bt;
+  if (out) {
+    out->waves = bt.waves;
+    out->tc = bt.tc > 0 ? bt.tc : ((ctx->prm.q >= 32) ? 16 : kstap::kTileCells);
+    out->ms_per_batch = best;
+  }
+  return KSTAP_OK;
+}
+
+kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* t) {
+  if (!ctx || !t) return KSTAP_EINVAL;
+  if (t->waves < 1 || t->waves > 64) return fail(ctx, KSTAP_EINVAL, "waves must be in [1, 64]");
+  if (t->tc != 0 && t->tc != 8 && t->tc != 16 && t->tc != 32)
+    return fail(ctx, KSTAP_EINVAL, "tc must be 0, 8, 16 or 32");
+  if (t->tc == 32 && ctx->prm.q >= 32)
+    return fail(ctx, KSTAP_EINVAL, "tc = 32 does not fit shared memory at q = 32");
+  ctx->tune.waves = t->waves;
+  ctx->tune.tc = t->tc;
+  return KSTAP_OK;
 }
 
 kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable) {
@@ -452,13 +839,14 @@ kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launch
 
 kstap_status kstap_destroy(kstap_ctx* ctx) {
   if (!ctx) return KSTAP_EINVAL;
-  if (ctx->ws || ctx->bank_aT) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws || ctx->bank_aT || ctx->jobs_dev) cudaStreamSynchronize(ctx->stream);
   for (int k = 0; k <= kstap_nkernels; ++k)
     if (ctx->ev[k][0]) {
       cudaEventDestroy(ctx->ev[k][0]);
       cudaEventDestroy(ctx->ev[k][1]);
     }
   cudaFree(ctx->ws);
+  cudaFree(ctx->jobs_dev);
   cudaFree(ctx->bank_aT);
   cudaFree(ctx->bank_bT);
   cudaFree(ctx->bank_n2);
@@ -478,14 +866,13 @@ const char* kstap_last_error(const kstap_ctx* ctx) {
 // lives in this file-scope device array instead of a cudaMalloc'd workspace.
 // Host code must not pass the array's name to a kernel: on the host it is only
 // a stand-in symbol.  The device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress and cached.  The B pass recomputes the lag sums (no lag
+// store), which keeps the array at ~16.5 MB.
 // ---------------------------------------------------------------------------
 #define KSTAP_NOALLOC_MAX_CELLS 32768
 #define KSTAP_NOALLOC_SCRATCH_BYTES (256 + (size_t)KSTAP_NOALLOC_MAX_CELLS * (45 + 9 + 9) * 8 + 1024)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KSTAP_NOALLOC_SCRATCH_BYTES];
-
-#include <mutex>
 
 namespace {
 
@@ -515,32 +902,6 @@ kstap_status noalloc_scratch(void** out) {
   return KSTAP_OK;
 }
 
-Geom noalloc_geom(const kstap_params& p, int H_in, int W_in) {
-  Geom g;
-  g.p = p.p;
-  g.q = p.q;
-  g.r_a = p.r_a;
-  g.r_b = p.r_b;
-  g.Rr = p.ring_r;
-  g.Ra = p.ring_a;
-  g.Gr = p.guard_r;
-  g.Ga = p.guard_a;
-  g.H_in = H_in;
-  g.W_in = W_in;
-  g.H = H_in - 2 * p.ring_r;
-  g.W = W_in - 2 * p.ring_a - p.q + 1;
-  const long nbox = (2L * p.ring_r + 1) * (2L * p.ring_a + 1);
-  g.n = (int)(nbox - (2L * p.guard_r + 1) * (2L * p.guard_a + 1));
-  g.V = 0;
-  g.B = (61 - ceil_log2(nbox)) / 2;
-  if (g.B > 26) g.B = 26;
-  g.max_iter = p.max_iter > 0 ? p.max_iter : 64;
-  g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
-  g.tau = p.tau;
-  g.tc = (p.q >= 32) ? 16 : kstap::kTileCells;
-  return g;
-}
-
 }  // namespace
 
 extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y,
@@ -555,20 +916,28 @@ extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, co
   if (H_in < 2 * params->ring_r + 1 || W_in < 2 * params->ring_a + params->q)
     return fail(nullptr, KSTAP_EINVAL, "frame %dx%d smaller than the training box plus window",
                 H_in, W_in);
-  const Geom g = noalloc_geom(*params, H_in, W_in);
-  const size_t ncell = (size_t)g.H * g.W;
+  const int H = H_in - 2 * params->ring_r, W = W_in - 2 * params->ring_a - params->q + 1;
+  const size_t ncell = (size_t)H * W;
   if (ncell > KSTAP_NOALLOC_MAX_CELLS)
     return fail(nullptr, KSTAP_EINVAL,
                 "frame has %zu cells; kstap_fit_project_noalloc handles at most %d cells "
                 "(use kstap_fit_project, or split the frame into tiles)",
                 ncell, KSTAP_NOALLOC_MAX_CELLS);
-  const WsLayout L = ws_layout(g.p, g.q, g.H, g.W, false);
+  const Layout L = make_layout(*params, {{H, W}}, false);
   if (L.total > KSTAP_NOALLOC_SCRATCH_BYTES)
     return fail(nullptr, KSTAP_EINVAL, "scratch layout %zu B exceeds the static %zu B", L.total,
                 (size_t)KSTAP_NOALLOC_SCRATCH_BYTES);
   void* scratch = nullptr;
   kstap_status st = noalloc_scratch(&scratch);
   if (st != KSTAP_OK) return st;
-  return dispatch_fit(nullptr, g, (const float2*)Y, (char*)scratch, L, false, factors,
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const Geom g = make_geom(*params, 0, 0);
+  std::vector<Frame> fr{Frame{Y, H_in, W_in, *factors, nullptr, nullptr, nullptr, nullptr}};
+  std::vector<Job> jobs;
+  JobList JL;
+  fill_jobs(*params, g, fr, (char*)scratch, &L, jobs, JL);
+  return dispatch_fit(nullptr, nullptr, g, JL, (char*)scratch, L, false, sms > 0 ? sms : 148, 4,
                       (cudaStream_t)cuda_stream);
 }

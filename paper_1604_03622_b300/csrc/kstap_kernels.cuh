@@ -38,7 +38,7 @@ namespace kstap {
 constexpr int kTileCells = 32;      // cells of one range row per CTA (moments / B passes)
 constexpr int kThreads = 256;
 constexpr int kRbMax = 4;
-constexpr float kBlind = 1e-2f;     // relative projected energy below which T_v is re-projected in FF
+constexpr float kBlindRefine = 1e-3f;   // |F_B b|^2 / |b|^2 below which w_b is refined in float-float
 constexpr float kLagNorm = 8.673617379884035e-19f;   // 2^-60: integer lag sums -> O(1) floats
 
 struct Geom {
@@ -53,6 +53,65 @@ struct Geom {
   float tau;
   int tc;         // cells per tile in the B pass
 };
+
+// One frame of a batch.  Per-cell workspace arrays of a launch are
+// struct-of-arrays over all cells of all jobs (stride NC), this job's cells
+// starting at cell0; its lag store starts at lag0 (float4 units).
+enum { kKindMoments = 0, kKindFlip = 1, kKindBfit = 2, kKindDetect = 3 };
+struct Job {
+  const float2* Y;
+  int H_in, W_in, H, W;
+  long long cell0, lag0;
+  unsigned* maxbits;            // 2 words: max |component| bits, non-finite flag
+  float2* UA;
+  float2* UBh;
+  float2* UBl;
+  float* lamA;
+  float* lamB;
+  int32_t* iters;
+  float* eta;
+  float* Tmax;
+  int32_t* vidx;
+  uint8_t* map;
+  float* T_all;
+  int tile0[4];                 // first tile of this job in each kernel's tile space
+};
+
+// A launch's jobs: one job passed by value (table == nullptr), or a device
+// table sorted by tile0.  ntiles = total tiles of each kernel kind.
+struct JobList {
+  Job one;
+  const Job* table;
+  int njobs;
+  int ntiles[4];
+  long long NC;                 // total cells (stride of the per-cell workspace arrays)
+};
+
+__device__ __forceinline__ const Job& job_of(const JobList& L, int kind, int tile, int& local) {
+  if (!L.table) {
+    local = tile;
+    return L.one;
+  }
+  int lo = 0, hi = L.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.table[mid].tile0[kind] <= tile)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  local = tile - L.table[lo].tile0[kind];
+  return L.table[lo];
+}
+
+__device__ __forceinline__ Geom with_job(const Geom& g0, const Job& J) {
+  Geom g = g0;
+  g.H_in = J.H_in;
+  g.W_in = J.W_in;
+  g.H = J.H;
+  g.W = J.W;
+  return g;
+}
 
 // ------------------------------------------------------------- helpers -----
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -98,8 +157,12 @@ __host__ __device__ constexpr int tri_idx(int n, int J, int Jp) {
 // ------------------------------------------------------- frame scale -------
 // max |component| of Y via the order-preserving bit pattern of non-negative
 // floats; non-finite values are recorded in *nonfinite.
-__global__ void k_frame_maxabs(const float* __restrict__ Y, size_t nfloat,
-                               unsigned* __restrict__ maxbits, unsigned* __restrict__ nonfinite) {
+__global__ void k_frame_maxabs(Geom g0, JobList L) {
+  const Job& J = L.table ? L.table[blockIdx.y] : L.one;
+  const float* __restrict__ Y = reinterpret_cast<const float*>(J.Y);
+  const size_t nfloat = 2 * (size_t)g0.p * J.H_in * J.W_in;
+  unsigned* maxbits = J.maxbits;
+  unsigned* nonfinite = J.maxbits + 1;
   unsigned m = 0, bad = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nfloat;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -223,15 +286,23 @@ constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
 // u in [c0, c0 + TC) (the last tile also its halo).
 template <int P, int Q>
 __global__ void __launch_bounds__(kMomThreads)
-k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
-          float2* __restrict__ Mw, float2* __restrict__ Sw, float4* __restrict__ Lw) {
+k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
+          float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NE = PP * (PP + 1) / 2;
   constexpr int TC = kTileCells;
   constexpr int TR = kMomRows;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int r0 = blockIdx.y * TR;
-  const int c0 = blockIdx.x * TC;
+  for (int tile = blockIdx.x; tile < JL.ntiles[kKindMoments]; tile += gridDim.x) {
+  int lt;
+  const Job& JB = job_of(JL, kKindMoments, tile, lt);
+  const Geom g = with_job(g0, JB);
+  const float2* __restrict__ Y = JB.Y;
+  const unsigned* __restrict__ maxbits = JB.maxbits;
+  float4* __restrict__ Lw = Lw0 ? Lw0 + JB.lag0 : nullptr;
+  const int ntx = (g.W + TC - 1) / TC;
+  const int r0 = (lt / ntx) * TR;
+  const int c0 = (lt % ntx) * TC;
   const int WT = TC + 2 * g.Ra + Q - 1;
   const int NR = 2 * g.Rr + 1;
   const int NRT = NR + TR - 1;
@@ -401,13 +472,15 @@ k_moments(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ max
     __syncthreads();
   }
   if (live) {
-    const size_t ncell = (size_t)g.H * g.W;
-    const size_t cell = (size_t)(r0 + tr) * g.W + (c0 + cl);
+    const size_t ncell = (size_t)JL.NC;
+    const size_t cell = (size_t)JB.cell0 + (size_t)(r0 + tr) * g.W + (c0 + cl);
 #pragma unroll
     for (int e = 0; e < NE; ++e) Mw[e * ncell + cell] = make_float2(wr[e], wi[e]);
 #pragma unroll
     for (int J = 0; J < PP; ++J) Sw[J * ncell + cell] = make_float2(sr[J], si[J]);
   }
+  __syncthreads();
+  }  // tile loop
 }
 
 // ------------------------------------------------ small Hermitian Jacobi ---
@@ -496,13 +569,22 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
 // U_A, lamA (tr A^ = p), iterations and eta.
 template <int P>
 __global__ void __launch_bounds__(128)
-k_flipflop(const float2* __restrict__ Mw, const float2* __restrict__ Sw, Geom g, size_t ncell,
-           float2* __restrict__ aw, float2* __restrict__ UA, float* __restrict__ lamA,
-           int32_t* __restrict__ iters, float* __restrict__ eta) {
+k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __restrict__ Sw,
+           float2* __restrict__ aw) {
   constexpr int PP = P * P;
   constexpr int NE = PP * (PP + 1) / 2;
-  const size_t cell = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (cell >= ncell) return;
+  const size_t ncell = (size_t)JL.NC;
+  for (int tile = blockIdx.x; tile < JL.ntiles[kKindFlip]; tile += gridDim.x) {
+  int lt;
+  const Job& JB = job_of(JL, kKindFlip, tile, lt);
+  const Geom& g = g0;
+  const size_t local = (size_t)lt * blockDim.x + threadIdx.x;
+  if (local >= (size_t)JB.H * JB.W) continue;
+  const size_t cell = (size_t)JB.cell0 + local;
+  float2* __restrict__ UA = JB.UA;
+  float* __restrict__ lamA = JB.lamA;
+  int32_t* __restrict__ iters = JB.iters;
+  float* __restrict__ eta = JB.eta;
   float2 M[NE];
 #pragma unroll
   for (int e = 0; e < NE; ++e) M[e] = Mw[e * ncell + cell];
@@ -607,17 +689,18 @@ k_flipflop(const float2* __restrict__ Mw, const float2* __restrict__ Sw, Geom g,
   for (int i = 0; i < P; ++i)
 #pragma unroll
     for (int m = 0; m < P; ++m)
-      if (m < ra) UA[(cell * P + i) * ra + m] = U[i][m];
+      if (m < ra) UA[(local * P + i) * ra + m] = U[i][m];
   if (lamA) {
 #pragma unroll
     for (int m = 0; m < P; ++m)
-      if (m < ra) lamA[cell * ra + m] = d[m] * sc;
+      if (m < ra) lamA[local * ra + m] = d[m] * sc;
   }
-  if (iters) iters[cell] = it;
+  if (iters) iters[local] = it;
   if (eta) {
     double e2 = (tr > 0.0 && an > 0.0) ? 1.0 - aMa / (an * tr) : 0.0;
-    eta[cell] = (float)sqrt(e2 > 0.0 ? e2 : 0.0);
+    eta[local] = (float)sqrt(e2 > 0.0 ? e2 : 0.0);
   }
+  }  // tile loop
 }
 
 // ------------------------------------------------ K3: B and U_B ------------
@@ -829,19 +912,28 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
 // whose static scratch has no room for the lag store).
 template <int P, int Q, int R, bool FROM_STORE>
 __global__ void __launch_bounds__(kThreads)
-k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbits,
-       const float2* __restrict__ aw, const float4* __restrict__ Lw, float2* __restrict__ UBh,
-       float2* __restrict__ UBl, float* __restrict__ lamB) {
+k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
   constexpr int CPW = 32 / Q;   // cells per warp in the eigen phase
   extern __shared__ __align__(16) unsigned char smem[];
+  for (int tile = blockIdx.x; tile < JL.ntiles[kKindBfit]; tile += gridDim.x) {
+  int lt;
+  const Job& JB = job_of(JL, kKindBfit, tile, lt);
+  const Geom g = with_job(g0, JB);
+  const float2* __restrict__ Y = JB.Y;
+  const unsigned* __restrict__ maxbits = JB.maxbits;
+  const float4* __restrict__ Lw = Lw0 ? Lw0 + JB.lag0 : nullptr;
+  float2* __restrict__ UBh = JB.UBh;
+  float2* __restrict__ UBl = JB.UBl;
+  float* __restrict__ lamB = JB.lamB;
   const int TC = g.tc;
-  const int r = blockIdx.y;
-  const int c0 = blockIdx.x * TC;
+  const int ntx = (g.W + TC - 1) / TC;
+  const int r = lt / ntx;
+  const int c0 = (lt % ntx) * TC;
   const int WT = TC + 2 * g.Ra + Q - 1;
   const int NUmax = TC + Q - 1;
-  const size_t ncell = (size_t)g.H * g.W;
+  const size_t ncell = (size_t)JL.NC;
   float4* Bs = reinterpret_cast<float4*>(smem);                 // [TC][NB]
   float2* as = reinterpret_cast<float2*>(Bs + TC * NB);         // [TC][PP]
   float4* lag = reinterpret_cast<float4*>(as + TC * PP);        // [PP][NUmax]
@@ -856,7 +948,8 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
   for (int idx = threadIdx.x; idx < TC * PP; idx += blockDim.x) {
     const int cl = idx / PP, J = idx % PP;
     const int c = c0 + cl;
-    as[idx] = (c < g.W) ? aw[J * ncell + (size_t)r * g.W + c] : make_float2(0.f, 0.f);
+    as[idx] = (c < g.W) ? aw[J * ncell + (size_t)JB.cell0 + (size_t)r * g.W + c]
+                        : make_float2(0.f, 0.f);
   }
   __syncthreads();
 
@@ -917,7 +1010,7 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
     float lam[R];
     eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
     if (live) {
-      const size_t cell = (size_t)r * g.W + (c0 + cl);
+      const size_t cell = (size_t)r * g.W + (c0 + cl);   // this job's cell index
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         UBh[(cell * Q + j) * R + m] = uh[m];
@@ -935,6 +1028,8 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
       }
     }
   }
+  __syncthreads();
+  }  // tile loop
 }
 
 // ------------------------------------------------ K4: detect ---------------
@@ -951,18 +1046,15 @@ k_bfit(const float2* __restrict__ Y, Geom g, const unsigned* __restrict__ maxbit
 // the error of T_v is ~2 eps sqrt(q) / sqrt(d^H P d / |d|^2).
 template <int P, int Q, int R>
 __global__ void __launch_bounds__(kThreads)
-k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_aT,
-         const float2* __restrict__ bank_bT, const float* __restrict__ bank_n2,
-         const float2* __restrict__ UA, const float2* __restrict__ UBh,
-         const float2* __restrict__ UBl, float* __restrict__ Tmax, int32_t* __restrict__ vidx,
-         uint8_t* __restrict__ map, float* __restrict__ T_all) {
+k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
+         const float2* __restrict__ bank_bT, const float* __restrict__ bank_n2) {
   constexpr int G = Q;                         // lanes per cell
   constexpr int CPW = 32 / G;                  // cells per warp
   constexpr int CPB = (kThreads / 32) * CPW;   // cells per block
   constexpr int VB = 4;                        // velocities per lane per pass
   constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 2 * P * R;   // float2 scratch per cell
   extern __shared__ __align__(16) unsigned char smem[];
-  const int V = g.V;
+  const int V = g0.V;
   float2* aT = reinterpret_cast<float2*>(smem);       // [P][V]
   float2* bT = aT + P * V;                             // [Q][V]
   float* na = reinterpret_cast<float*>(bT + Q * V);    // [V]
@@ -975,7 +1067,16 @@ k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_a
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / G, gl = lane % G;
   const int slot = warp * CPW + sub;
-  const size_t cell = (size_t)blockIdx.x * CPB + slot;
+  for (int tile = blockIdx.x; tile < JL.ntiles[kKindDetect]; tile += gridDim.x) {
+  int lt;
+  const Job& JB = job_of(JL, kKindDetect, tile, lt);
+  const Geom g = with_job(g0, JB);
+  const float2* __restrict__ Y = JB.Y;
+  const float2* __restrict__ UA = JB.UA;
+  const float2* __restrict__ UBh = JB.UBh;
+  const float2* __restrict__ UBl = JB.UBl;
+  float* __restrict__ T_all = JB.T_all;
+  const size_t cell = (size_t)lt * CPB + slot;
   const size_t ncell = (size_t)g.H * g.W;
   const bool live = cell < ncell;
   float2* Xs = scr + slot * CS;        // [P][Q]
@@ -1101,6 +1202,38 @@ k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_a
           }
         }
       }
+      // Nearly blind velocities (|F_B b|^2 < 1e-3 |b|^2): redo w_b = b - U G with
+      // the subtraction in float-float and the low part of U_B included.  Errors
+      // of G itself lie in span(U_B), which Z annihilates, so G stays FP32.
+#pragma unroll
+      for (int k = 0; k < VB; ++k) {
+        if (k < nv && dB[k] < kBlindRefine * nb[v0 + k]) {
+          float dBn = 0.f;
+#pragma unroll
+          for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
+          for (int j = 0; j < Q; ++j) {
+            const float2 b = bT[j * V + v0 + k];
+            float sr = b.x, cr = 0.f, si = b.y, ci = 0.f;
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+              const float2 u = Uh[j * R + m], ul = Ul[j * R + m], G = Gm[k][m];
+              acc_prod(sr, cr, -u.x, G.x);   // re -= ur Gr - ui Gi
+              acc_prod(sr, cr, u.y, G.y);
+              acc_prod(si, ci, -u.x, G.y);   // im -= ur Gi + ui Gr
+              acc_prod(si, ci, -u.y, G.x);
+              cr = __fmaf_rn(-ul.x, G.x, cr);
+              cr = __fmaf_rn(ul.y, G.y, cr);
+              ci = __fmaf_rn(-ul.x, G.y, ci);
+              ci = __fmaf_rn(-ul.y, G.x, ci);
+            }
+            const float2 w = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+            dBn += cabs2(w);
+#pragma unroll
+            for (int i = 0; i < P; ++i) y[k][i] = cadd(y[k][i], cmul(Zs[i * Q + j], cconj(w)));
+          }
+          dB[k] = dBn;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
         if (k >= nv) break;
@@ -1137,10 +1270,12 @@ k_detect(const float2* __restrict__ Y, Geom g, const float2* __restrict__ bank_a
     }
   }
   if (live && gl == 0) {
-    Tmax[cell] = best;
-    vidx[cell] = bestv;
-    map[cell] = (best > g.tau) ? 1 : 0;
+    JB.Tmax[cell] = best;
+    JB.vidx[cell] = bestv;
+    JB.map[cell] = (best > g.tau) ? 1 : 0;
   }
+  __syncwarp();
+  }  // tile loop
 }
 
 }  // namespace kstap

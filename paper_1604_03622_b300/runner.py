@@ -63,6 +63,21 @@ class KStap:
             self._bufs[key] = b
         return self._bufs[key]
 
+    def alloc_outputs(self, H_in, W_in, T_all=False) -> Dict[str, torch.Tensor]:
+        """Fresh (not cached) factor and output buffers for one frame."""
+        key_bufs = self._bufs.pop((H_in, W_in, T_all), None)
+        b = self.buffers(H_in, W_in, T_all)
+        self._bufs.pop((H_in, W_in, T_all), None)
+        if key_bufs is not None:
+            self._bufs[(H_in, W_in, T_all)] = key_bufs
+        return b
+
+    def frame_desc(self, Y: torch.Tensor, b: Dict[str, torch.Tensor]):
+        from . import make_frame
+        _, H_in, W_in = Y.shape
+        return make_frame(Y, H_in, W_in, b["factors"], b["Tmax"], b["vidx"], b["map"],
+                          b.get("T_all"))
+
     def run(self, Y: torch.Tensor, T_all: bool = False) -> Dict[str, torch.Tensor]:
         """fit_project + detect on a device frame Y (p, H_in, W_in) complex64."""
         assert Y.is_cuda and Y.dtype == torch.complex64 and Y.is_contiguous()
