@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-plain leg on the 256-tile workload")
     ap.add_argument("--cells", type=int, nargs=2, metavar=("H", "W"),
                     help="run the workload's model on an H x W cell grid (profiling cases)")
     return ap.parse_args()
@@ -175,6 +177,76 @@ def work_per_cell(wl):
                 bfit=lag_per_cell + b_flops + eig_flops, detect=det_flops)
 
 
+# ------------------------------------------------------- batched vs plain ---
+def batched_leg(dev, steps: int, warmup: int):
+    """256 uneven tiles (q in {8,16,32}, r_b in {2,3,4}): plain = one tile at a
+    time through kstap_fit_project + kstap_detect (5 launches per tile, no
+    overlap); batched = one CUDA graph holding one autotuned batch per (q, r_b)
+    class on parallel branches.  Both compute the same bits (tested)."""
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    tiles = gen.tile_batch()
+    frames = [gen.make_frame(w) for w in tiles]
+    classes = {}
+    for i, w in enumerate(tiles):
+        classes.setdefault((w.q, w.r_b), []).append(i)
+    keys = sorted(classes)
+    ctxs, descs, bufs, Ys = {}, {}, {}, [None] * len(tiles)
+    for key in keys:
+        idx = classes[key]
+        ks = KStap.from_workload(tiles[idx[0]], frames[idx[0]].bank_a, frames[idx[0]].bank_b,
+                                 device=str(dev))
+        ctxs[key] = ks
+        for i in idx:
+            Ys[i] = torch.from_numpy(frames[i].Y).to(dev)
+        # the descriptors hold raw device pointers: keep the tensors alive
+        bufs[key] = [ks.alloc_outputs(Ys[i].shape[1], Ys[i].shape[2]) for i in idx]
+        descs[key] = [ks.frame_desc(Ys[i], b) for i, b in zip(idx, bufs[key])]
+    stream = torch.cuda.current_stream(dev)
+    tuning = {}
+    for key in keys:
+        t = K.kstap_autotune(ctxs[key].ctx, descs[key], reps=2)
+        tuning[f"q{key[0]}_r{key[1]}"] = dict(waves=t.waves, tc=t.tc, ms=round(t.ms_per_batch, 3))
+    graph = K.kstap_graph_create([ctxs[k].ctx for k in keys], [descs[k] for k in keys])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ncells = sum(w.cells for w in tiles)
+
+    def timed(fn):
+        out = []
+        for s in range(warmup + steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if s >= warmup:
+                out.append(a.elapsed_time(b))
+        return out
+
+    def plain():
+        for key in keys:
+            ks = ctxs[key]
+            for i in classes[key]:
+                ks.run(Ys[i])
+
+    plain_ms = timed(plain)
+    batched_ms = timed(lambda: K.kstap_graph_launch(graph, stream.cuda_stream))
+    K.kstap_graph_destroy(graph)
+    for ks in ctxs.values():
+        ks.close()
+    pm, bm = sum(plain_ms) / len(plain_ms), sum(batched_ms) / len(batched_ms)
+    return dict(workload="tiles256", tiles=len(tiles), cells=ncells, classes=len(keys),
+                plain=dict(cells_per_s=ncells / (pm / 1e3), ms_per_batch=pm,
+                           p99_ms=sorted(plain_ms)[-1], kernel_launches=5 * len(tiles)),
+                batched=dict(cells_per_s=ncells / (bm / 1e3), ms_per_batch=bm,
+                             p99_ms=sorted(batched_ms)[-1], graph_launches=1,
+                             kernel_launches=5 * len(keys)),
+                speedup=pm / bm, tuning=tuning)
+
+
 # ------------------------------------------------------------------ main ----
 def main():
     args = parse()
@@ -287,6 +359,9 @@ def main():
                 kernel_share={k: v[0] / max(sum(x[0] for x in kt.values()), 1e-9)
                               for k, v in kt.items()})
 
+    batched = None if args.no_batched else batched_leg(dev, max(3, min(args.steps, 10)),
+                                                         max(2, args.warmup))
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -313,7 +388,8 @@ def main():
                                           d2h_bytes_per_step=d2h,
                                           ms_per_step=e2e_total / args.steps),
         gpu_launches=sum(v[1] for v in kt.values()),
-        roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall)
+        roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
+        batched=batched)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

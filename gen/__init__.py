@@ -224,3 +224,21 @@ def random_cells(wl: Workload, count: int, seed: int) -> np.ndarray:
     total = wl.H * wl.W
     count = min(count, total)
     return np.sort(rng.choice(total, size=count, replace=False)).astype(np.int64)
+
+
+def tile_batch(n_tiles: int = 256, seed: int = SEED_BASE + 2, V: int = 64,
+               cnr_db: float = 40.0) -> List[Workload]:
+    """Uneven frame tiles: H ~ logU[32, 512], W ~ logU[32, 384] cells, q uniform
+    in {8, 16, 32}, r_b uniform in {2, 3, 4}, n = 2pq training cells (p = 3),
+    V velocities, targets at the density of the 1024^2 frame (200 per 1M cells)."""
+    rng = np.random.default_rng([seed, STREAM_SIZES])
+    out = []
+    for k in range(n_tiles):
+        H = int(round(math.exp(rng.uniform(math.log(32), math.log(512)))))
+        W = int(round(math.exp(rng.uniform(math.log(32), math.log(384)))))
+        q = int(rng.choice([8, 16, 32]))
+        r_b = int(rng.choice([2, 3, 4]))
+        nt = max(1, int(round(200 * H * W / 1048576.0)))
+        out.append(make_workload(f"tile{k:03d}", H, W, q, r_b, 2 * 3 * q, V, cnr_db, nt,
+                                 (0.0, 15.0), 1000 + k))
+    return out

@@ -73,6 +73,8 @@ class KStap:
         return b
 
     def frame_desc(self, Y: torch.Tensor, b: Dict[str, torch.Tensor]):
+        """Batch descriptor of frame Y with output buffers b.  It holds raw
+        device pointers: the caller keeps Y and b alive while it is used."""
         from . import make_frame
         _, H_in, W_in = Y.shape
         return make_frame(Y, H_in, W_in, b["factors"], b["Tmax"], b["vidx"], b["map"],
