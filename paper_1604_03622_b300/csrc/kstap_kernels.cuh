@@ -772,12 +772,15 @@ __device__ __forceinline__ void orthonormalise_g(float2 (&x)[R]) {
 }
 
 // Leading R-dimensional eigenspace of one cell's B (group of Q lanes, lane j
-// = row j): FP32 subspace iteration on B_hi until the invariant-subspace
-// residual |BV - V V^H B V| <= 2e-6 |BV| (all cells of the warp), then
-// float-float subspace steps Y = B V with Cholesky-QR; a second step runs
-// only while the first still moved the subspace by > 1e-6.  Loop exits are
-// warp-uniform because several cells share a warp.  `live` = this group's
-// cell exists; dead groups compute on zeros.
+// = row j).  Start: R columns of B (they lie mostly in the clutter subspace),
+// orthonormalised; one FP32 subspace step on B_hi; then float-float subspace
+// steps Y = B V with Cholesky-QR, U = Y L^-H.  Each float-float step measures
+// how far it moved the subspace, |U - V V^H U|_F = |(Y - V H) L^-H|_F with
+// H = V^H Y (also the Ritz matrix), and the loop stops once that change is
+// below 1e-6 (the next step would move it by a further factor
+// lambda_{R+1} / lambda_R).  The Ritz values are the eigenvalues of the last
+// V^H B V.  Loop exits are warp-uniform because several cells share a warp;
+// `live` = this group's cell exists (dead groups compute on zeros).
 template <int Q, int R>
 __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live,
                                  float2* __restrict__ Vs, float2 (&uh)[R], float2 (&ul)[R],
@@ -789,44 +792,18 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     v[m] = make_float2(b.x, b.z);
   }
   orthonormalise_g<Q, R>(v);
-  float2 H[R][R];   // V^H B V of the last iteration (its eigenvalues are the Ritz values)
-  for (int it = 0; it < 48; ++it) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
-    __syncwarp();
-    b_times_v_fp32<Q, R>(Bc, j, Vs, y);
-    __syncwarp();
-    float ry = 0.f, re = 0.f;
+  for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+  __syncwarp();
+  b_times_v_fp32<Q, R>(Bc, j, Vs, y);
+  __syncwarp();
+  orthonormalise_g<Q, R>(y);
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      float2 e = y[m];
-#pragma unroll
-      for (int mp = 0; mp < R; ++mp) {
-        H[mp][m] = grp_sum2<Q>(cmulc(v[mp], y[m]));
-        e = csub(e, cmul(v[mp], H[mp][m]));
-      }
-      ry += cabs2(y[m]);
-      re += cabs2(e);
-    }
-    ry = grp_sum<Q>(ry);
-    re = grp_sum<Q>(re);
-    orthonormalise_g<Q, R>(y);
-#pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = y[m];
-    const bool done = !live || re <= 4e-12f * ry || !(ry > 0.f);
-    if (__all_sync(0xffffffffu, done)) break;
-  }
-  // Ritz values (FP32) for reporting: eigenvalues of V^H B V of the converged
-  // iteration (accurate to the square of its residual)
-  {
-    float dd[R];
-    float2 UU[R][R];
-    jacobi_small<R>(H, dd, UU);
-#pragma unroll
-    for (int m = 0; m < R; ++m) lam[m] = dd[m];
-  }
+  for (int m = 0; m < R; ++m) v[m] = y[m];
+
   cff U[R];
-  for (int step = 0; step < 3; ++step) {
+  float2 H[R][R];
+  for (int step = 0; step < 4; ++step) {
 #pragma unroll
     for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
     __syncwarp();
@@ -850,7 +827,12 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     cff Yf[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) Yf[m] = cff{ff_make(s[m][0], s[m][1]), ff_make(s[m][2], s[m][3])};
-    // Gram G = Y^H Y, Cholesky G = L L^H, U = Y L^-H (float-float)
+    // H = V^H Y (FP32), Gram G = Y^H Y (float-float)
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp)
+        H[m][mp] = grp_sum2<Q>(cmulc(v[m], make_float2(Yf[mp].re.hi, Yf[mp].im.hi)));
     cff Gm[R][R];
 #pragma unroll
     for (int m = 0; m < R; ++m)
@@ -859,6 +841,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
         const cff pr = cff_cmul(Yf[m], Yf[mp]);
         Gm[m][mp] = cff{grp_sum_ff<Q>(pr.re), grp_sum_ff<Q>(pr.im)};
       }
+    // Cholesky G = L L^H
     cff L[R][R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
@@ -876,6 +859,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
         L[i][m] = cff{ff_div(t.re, lmm), ff_div(t.im, lmm)};
       }
     }
+    // U = Y L^-H (row j)
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       cff t = Yf[m];
@@ -884,21 +868,41 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
       const ff lmm = L[m][m].re;
       U[m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
     }
-    // change of the subspace in this step: |U - V V^H U|_F (single precision)
-    float change = 0.f;
+    // change of the subspace: (I - V V^H) U = (Y - V H) L^-H, row j (FP32;
+    // the residual is formed directly, so small changes do not cancel)
+    float local = 0.f;
+    {
+      float2 X[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      const float2 um = make_float2(U[m].re.hi, U[m].im.hi);
-      float2 e = um;
+      for (int m = 0; m < R; ++m) {
+        float2 t = make_float2(Yf[m].re.hi, Yf[m].im.hi);
 #pragma unroll
-      for (int mp = 0; mp < R; ++mp) e = csub(e, cmul(v[mp], grp_sum2<Q>(cmulc(v[mp], um))));
-      change += cabs2(e);
+        for (int mp = 0; mp < R; ++mp) t = csub(t, cmul(v[mp], H[mp][m]));
+#pragma unroll
+        for (int k = 0; k < m; ++k) t = csub(t, cmul(X[k], make_float2(L[m][k].re.hi, -L[m][k].im.hi)));
+        const float lmm = L[m][m].re.hi;
+        X[m] = (lmm > 0.f) ? cscale(t, 1.f / lmm) : make_float2(0.f, 0.f);
+        local += cabs2(X[m]);
+      }
     }
-    change = grp_sum<Q>(change);
+    const float change = grp_sum<Q>(local);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
     const bool done = !live || change < 1e-12f;
     if (__all_sync(0xffffffffu, done)) break;
+  }
+  // Ritz values: eigenvalues of V^H B V of the last step (FP32)
+  {
+    float2 Hh[R][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp) Hh[m][mp] = H[m][mp];
+    float dd[R];
+    float2 UU[R][R];
+    jacobi_small<R>(Hh, dd, UU);
+#pragma unroll
+    for (int m = 0; m < R; ++m) lam[m] = dd[m];
   }
 #pragma unroll
   for (int m = 0; m < R; ++m) {
@@ -907,9 +911,6 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   }
 }
 
-// FROM_STORE: read the float-float lag sums written by k_moments (Lw);
-// otherwise recompute them from Y (used by the allocation-free entry point,
-// whose static scratch has no room for the lag store).
 template <int P, int Q, int R, bool FROM_STORE>
 __global__ void __launch_bounds__(kThreads)
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
