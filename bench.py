@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg on the 256-tile workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="requests in the Poisson serving stream")
     ap.add_argument("--cells", type=int, nargs=2, metavar=("H", "W"),
                     help="run the workload's model on an H x W cell grid (profiling cases)")
     return ap.parse_args()
@@ -247,6 +250,94 @@ def batched_leg(dev, steps: int, warmup: int):
                 speedup=pm / bm, tuning=tuning)
 
 
+# ----------------------------------------------------------------- serving ---
+def serving_leg(dev, n_requests: int):
+    """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
+    V = 64) at 0.8 x the measured plain capacity, through kstap_submit /
+    kstap_poll with a 120 GB HBM budget (60 GB per q class).  plain: one frame
+    at a time (batch 1, one stream); batched: continuous batching (batch <= 16,
+    4 streams).  Latency = completion - arrival."""
+    import threading
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    pool = gen.serving_pool()
+    frames = [gen.make_frame(w) for w in pool]
+    Ys = [torch.from_numpy(f.Y).to(dev) for f in frames]
+    qs = sorted({w.q for w in pool})
+    budget = 120 << 30
+    # plain capacity: mean per-frame time of the plain path over the pool
+    per_frame_s = []
+    for q in qs:
+        idx = [i for i, w in enumerate(pool) if w.q == q]
+        ks = KStap.from_workload(pool[idx[0]], frames[idx[0]].bank_a, frames[idx[0]].bank_b,
+                                 device=str(dev))
+        for i in idx:
+            ks.run(Ys[i])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ks.run(Ys[i])
+            b.record()
+            b.synchronize()
+            per_frame_s.append(a.elapsed_time(b) / 1e3)
+        ks.close()
+    rate = 0.8 / float(np.mean(per_frame_s))
+    t_arr, pick = gen.poisson_arrivals(n_requests, rate, len(pool))
+
+    def run(max_batch, max_inflight):
+        ctxs = {}
+        for q in qs:
+            i0 = [i for i, w in enumerate(pool) if w.q == q][0]
+            ks = KStap.from_workload(pool[i0], frames[i0].bank_a, frames[i0].bank_b,
+                                     device=str(dev), hbm_budget_bytes=budget // len(qs))
+            K.kstap_serve_config(ks.ctx, max_batch, max_inflight)
+            ctxs[q] = ks
+        tickets = [None] * n_requests
+        t0 = time.perf_counter()
+        sub_us = [0.0] * n_requests
+
+        def submitter():
+            for k in range(n_requests):
+                dt = t_arr[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                i = int(pick[k])
+                ks = ctxs[pool[i].q]
+                tickets[k] = (ks, K.kstap_submit(ks.ctx, Ys[i], Ys[i].shape[1], Ys[i].shape[2]))
+                sub_us[k] = (time.perf_counter() - t0) * 1e6
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, cells, t_end = [], 0, 0.0
+        for k in range(n_requests):
+            while tickets[k] is None:
+                time.sleep(1e-4)
+            ks, tk = tickets[k]
+            r = K.kstap_poll(ks.ctx, tk, timeout_us=-1)
+            lat.append((r.t_done_us - r.t_submit_us) / 1e3)
+            cells += r.H * r.W
+            K.kstap_release(ks.ctx, tk)
+        t_end = time.perf_counter() - t0
+        th.join()
+        for ks in ctxs.values():
+            ks.close()
+        lat = sorted(lat)
+        return dict(cells_per_s=cells / t_end, p50_ms=lat[len(lat) // 2],
+                    p99_ms=lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                    mean_ms=float(np.mean(lat)), wall_s=t_end, max_batch=max_batch,
+                    streams=max_inflight)
+
+    plain = run(1, 1)
+    batched = run(16, 4)
+    return dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
+                q=qs, r_b=3, V=64, budget_gb=120, arrival_rate_hz=rate,
+                plain_capacity_frames_per_s=1.0 / float(np.mean(per_frame_s)),
+                mean_cells_per_frame=float(np.mean([pool[int(i)].cells for i in pick])),
+                plain=plain, batched=batched)
+
+
 # ------------------------------------------------------------------ main ----
 def main():
     args = parse()
@@ -362,6 +453,8 @@ def main():
     batched = None if args.no_batched else batched_leg(dev, max(3, min(args.steps, 10)),
                                                          max(2, args.warmup))
 
+    serving = None if args.no_serving else serving_leg(dev, args.serve_requests)
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -389,7 +482,7 @@ def main():
                                           ms_per_step=e2e_total / args.steps),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
-        batched=batched)
+        batched=batched, serving=serving)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

@@ -242,3 +242,27 @@ def tile_batch(n_tiles: int = 256, seed: int = SEED_BASE + 2, V: int = 64,
         out.append(make_workload(f"tile{k:03d}", H, W, q, r_b, 2 * 3 * q, V, cnr_db, nt,
                                  (0.0, 15.0), 1000 + k))
     return out
+
+
+def serving_pool(n_per_q: int = 4, seed: int = SEED_BASE + 4, V: int = 64,
+                 qs=(16, 32), r_b: int = 3, lo: int = 256, hi: int = 4096) -> List[Workload]:
+    """Frames for the serving stream: sides uniform in [lo, hi] cells, q in qs,
+    r_b = 3, n = 2pq, V velocities, 40 dB CNR, targets at the 1024^2 density."""
+    rng = np.random.default_rng([seed, STREAM_SIZES])
+    out = []
+    for q in qs:
+        for k in range(n_per_q):
+            H = int(rng.integers(lo, hi + 1))
+            W = int(rng.integers(lo, hi + 1))
+            nt = max(1, int(round(200 * H * W / 1048576.0)))
+            out.append(make_workload(f"serve_q{q}_{k}", H, W, q, r_b, 2 * 3 * q, V, 40.0, nt,
+                                     (0.0, 15.0), 2000 + 10 * q + k))
+    return out
+
+
+def poisson_arrivals(n: int, rate_hz: float, n_frames: int, seed: int = SEED_BASE + 5):
+    """Arrival times (s) of a Poisson stream and the pool index of each request."""
+    rng = np.random.default_rng([seed, STREAM_SIZES])
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+    idx = rng.integers(0, n_frames, size=n)
+    return t, idx

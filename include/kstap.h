@@ -208,6 +208,44 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
                             kstap_tuning* out);
 kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* tuning);
 
+/* ------------------------------------------------------------ serving ----
+ * A request loop over the context: kstap_submit queues a frame and returns a
+ * ticket at once; a worker thread admits queued frames in arrival order while
+ * their device memory (workspace, factors and, for host frames, a device copy)
+ * fits the context's HBM budget, groups whatever is admissible into one
+ * batch (same kernels and results as kstap_run_batch) and enqueues it on one
+ * of max_inflight streams, so batches overlap on the device and frames that
+ * arrive meanwhile join the next batch.  Device frames are borrowed until
+ * their request completes; host frames are copied at admission.  Results
+ * (Tmax, vidx, map on the device, H * W cells) are held until kstap_release.
+ * Results count against the budget from submit until release, so unreleased
+ * results throttle admission.  Budget 0 = unlimited; a frame larger than the
+ * budget is refused at submit (KSTAP_ENOMEM).  While a context serves, do not
+ * call its other entry points from other threads. */
+#define KSTAP_FRAME_ON_HOST 1
+typedef struct {
+  uint64_t ticket;
+  int H, W;                 /* cell grid */
+  const float* Tmax;        /* device, library-owned until kstap_release */
+  const int32_t* vidx;
+  const uint8_t* map;
+  double t_submit_us;       /* microseconds since the context's first submit */
+  double t_admit_us;
+  double t_done_us;         /* completion (host callback after the last kernel) */
+} kstap_result;
+
+/* Serving limits: frames per batch (1..1024, default 16) and batches in
+ * flight (1..16, default 4).  Call before the first kstap_submit. */
+kstap_status kstap_serve_config(kstap_ctx* ctx, int max_batch, int max_inflight);
+/* flags: KSTAP_FRAME_ON_HOST when Y is in host memory (pinned for overlap). */
+kstap_status kstap_submit(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in, int flags,
+                          uint64_t* ticket);
+/* timeout_us: 0 = non-blocking (KSTAP_EAGAIN if not done), < 0 = wait,
+ * > 0 = wait at most that long (KSTAP_ETIMEOUT). */
+kstap_status kstap_poll(kstap_ctx* ctx, uint64_t ticket, kstap_result* out, int timeout_us);
+/* Frees a completed request's results (KSTAP_EAGAIN while in flight). */
+kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket);
+
 /* Allocation-free variant of kstap_fit_project.  The paper has no
  * counterpart: this exists for callers that must not allocate device memory
  * while they run -- for example a real-time processing loop, where cudaMalloc

@@ -22,7 +22,8 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_last_error", "kstap_workspace_bytes", "kstap_set_profiling",
             "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
-            "kstap_set_tuning"]
+            "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
+            "kstap_release"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -47,6 +48,16 @@ class KstapFrame(ctypes.Structure):
 
 class KstapTuning(ctypes.Structure):
     _fields_ = [("waves", ctypes.c_int), ("tc", ctypes.c_int), ("ms_per_batch", ctypes.c_float)]
+
+
+class KstapResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("Tmax", ctypes.c_void_p), ("vidx", ctypes.c_void_p), ("map", ctypes.c_void_p),
+                ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
+
+
+KSTAP_FRAME_ON_HOST = 1
 
 
 class KstapError(RuntimeError):
@@ -86,12 +97,17 @@ def lib() -> ctypes.CDLL:
         L.kstap_autotune.argtypes = [P, ctypes.POINTER(KstapFrame), I, I,
                                      ctypes.POINTER(KstapTuning)]
         L.kstap_set_tuning.argtypes = [P, ctypes.POINTER(KstapTuning)]
+        L.kstap_serve_config.argtypes = [P, I, I]
+        L.kstap_submit.argtypes = [P, P, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
+        L.kstap_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KstapResult), I]
+        L.kstap_release.argtypes = [P, ctypes.c_uint64]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
         for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
                      "kstap_set_profiling", "kstap_kernel_times", "kstap_fit_project_noalloc",
                      "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
-                     "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning"):
+                     "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
+                     "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -211,3 +227,29 @@ def kstap_autotune(ctx: int, frames, reps: int = 3) -> KstapTuning:
 def kstap_set_tuning(ctx: int, waves: int, tc: int = 0) -> None:
     t = KstapTuning(waves, tc, 0.0)
     _check(lib().kstap_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def kstap_serve_config(ctx: int, max_batch: int, max_inflight: int) -> None:
+    _check(lib().kstap_serve_config(ctx, max_batch, max_inflight), ctx)
+
+
+def kstap_submit(ctx: int, Y, H_in: int, W_in: int, on_host: bool = False) -> int:
+    """Queue one frame (torch tensor; pinned host tensor when on_host)."""
+    t = ctypes.c_uint64()
+    _check(lib().kstap_submit(ctx, _ptr(Y), H_in, W_in, KSTAP_FRAME_ON_HOST if on_host else 0,
+                              ctypes.byref(t)), ctx)
+    return int(t.value)
+
+
+def kstap_poll(ctx: int, ticket: int, timeout_us: int = -1):
+    """KstapResult when done; None if not ready (timeout_us = 0) or timed out."""
+    r = KstapResult()
+    st = lib().kstap_poll(ctx, ticket, ctypes.byref(r), timeout_us)
+    if st in (-4, -5):
+        return None
+    _check(st, ctx)
+    return r
+
+
+def kstap_release(ctx: int, ticket: int) -> None:
+    _check(lib().kstap_release(ctx, ticket), ctx)

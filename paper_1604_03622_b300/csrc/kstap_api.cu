@@ -7,7 +7,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +27,7 @@ using kstap::Geom;
 using kstap::Job;
 using kstap::JobList;
 
+struct Server;
 namespace {
 struct Tuning {
   int waves = 4;   // persistent grid = SMs x resident CTAs x waves (capped by tiles)
@@ -53,6 +59,7 @@ struct kstap_ctx {
   float kernel_ms[kstap_nkernels] = {};
   int kernel_launches[kstap_nkernels] = {};
   bool ev_pending[kstap_nkernels] = {};
+  struct Server* server = nullptr;   // created by the first kstap_submit
 };
 
 struct kstap_graph {
@@ -233,7 +240,11 @@ int tiles_detect(int H, int W, int q) {
   return (int)(((size_t)H * W + c - 1) / c);
 }
 
-// A frame as the library sees it (device pointers, caller-owned).
+// A frame (or a row strip of one) as the library sees it (device pointers,
+// caller-owned).  ch_stride: elements between channel planes (0 = H_in * W_in).
+// A strip takes its own fixed-point scale (max over its rows), so its results
+// agree with the whole frame's to rounding (within the parity tolerance), and
+// a given split is deterministic.
 struct Frame {
   const kstap_c64* Y;
   int H_in, W_in;
@@ -242,7 +253,39 @@ struct Frame {
   int32_t* vidx;
   uint8_t* map;
   float* T_all;
+  long long ch_stride = 0;
 };
+
+// Row strips of at most `rows` cell rows.  Strip k covers cell rows
+// [r0, r0 + nr) and reads input rows [r0, r0 + nr + 2 ring_r) of every
+// channel; its factor and output pointers are offset to cell r0 * W.
+std::vector<Frame> split_rows(const kstap_params& p, int V, const Frame& f, int rows) {
+  std::vector<Frame> out;
+  const int H = f.H_in - 2 * p.ring_r, W = f.W_in - 2 * p.ring_a - p.q + 1;
+  const long long cs = f.ch_stride ? f.ch_stride : (long long)f.H_in * f.W_in;
+  for (int r0 = 0; r0 < H; r0 += rows) {
+    const int nr = std::min(rows, H - r0);
+    const size_t c0 = (size_t)r0 * W;
+    Frame s = f;
+    s.Y = f.Y + (size_t)r0 * f.W_in;
+    s.H_in = nr + 2 * p.ring_r;
+    s.ch_stride = cs;
+    auto off = [&](auto* ptr, size_t per) { return ptr ? ptr + c0 * per : ptr; };
+    s.f.UA = off(f.f.UA, (size_t)p.p * p.r_a);
+    s.f.UB_hi = off(f.f.UB_hi, (size_t)p.q * p.r_b);
+    s.f.UB_lo = off(f.f.UB_lo, (size_t)p.q * p.r_b);
+    s.f.lamA = off(f.f.lamA, (size_t)p.r_a);
+    s.f.lamB = off(f.f.lamB, (size_t)p.r_b);
+    s.f.iters = off(f.f.iters, 1);
+    s.f.eta = off(f.f.eta, 1);
+    s.Tmax = off(f.Tmax, 1);
+    s.vidx = off(f.vidx, 1);
+    s.map = off(f.map, 1);
+    s.T_all = off(f.T_all, (size_t)V);
+    out.push_back(s);
+  }
+  return out;
+}
 
 // Fills the jobs of one launch; scratch and L may be null (detect-only).
 void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& fr, char* scratch,
@@ -255,6 +298,7 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
     j.Y = (const float2*)fr[k].Y;
     j.H_in = fr[k].H_in;
     j.W_in = fr[k].W_in;
+    j.ch_stride = fr[k].ch_stride ? fr[k].ch_stride : (long long)fr[k].H_in * fr[k].W_in;
     j.H = fr[k].H_in - 2 * p.ring_r;
     j.W = fr[k].W_in - 2 * p.ring_a - p.q + 1;
     j.cell0 = L ? (long long)L->cell0[k] : 0;
@@ -583,16 +627,36 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
   if (st != KSTAP_OK) return st;
   const kstap_params& p = ctx->prm;
   const int H = H_in - 2 * p.ring_r, W = W_in - 2 * p.ring_a - p.q + 1;
-  const Layout L = make_layout(p, {{H, W}}, true);
-  st = ensure_ws(ctx, L.total);
-  if (st != KSTAP_OK) return st;
   const Geom g = make_geom(p, ctx->V, ctx->tune.tc);
-  std::vector<Frame> fr{Frame{Y, H_in, W_in, *factors, nullptr, nullptr, nullptr, nullptr}};
-  std::vector<Job> jobs;
-  JobList JL;
-  fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
-  return dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
+  const Frame whole{Y, H_in, W_in, *factors, nullptr, nullptr, nullptr, nullptr};
+  // A frame whose workspace exceeds the budget runs as row strips, one after
+  // the other on the stream, in one strip-sized workspace.
+  int rows = H;
+  const size_t full = make_layout(p, {{H, W}}, true).total;
+  if (ctx->budget && full > ctx->budget) {
+    const size_t per_row = std::max<size_t>(1, make_layout(p, {{1, W}}, true).total);
+    rows = (int)std::max<size_t>(kstap::kMomRows, ctx->budget / per_row);
+    rows -= rows % kstap::kMomRows;
+    if (make_layout(p, {{std::min(rows, H), W}}, true).total > ctx->budget)
+      return fail(ctx, KSTAP_ENOMEM, "a %d-row strip of this frame exceeds the HBM budget %zu B",
+                  kstap::kMomRows, ctx->budget);
+  }
+  const std::vector<Frame> strips = (rows >= H) ? std::vector<Frame>{whole}
+                                                : split_rows(p, ctx->V, whole, rows);
+  for (const Frame& s : strips) {
+    const int sh = s.H_in - 2 * p.ring_r;
+    const Layout L = make_layout(p, {{sh, W}}, true);
+    st = ensure_ws(ctx, L.total);
+    if (st != KSTAP_OK) return st;
+    std::vector<Frame> fr{s};
+    std::vector<Job> jobs;
+    JobList JL;
+    fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
+    st = dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
                       ctx->stream);
+    if (st != KSTAP_OK) return st;
+  }
+  return KSTAP_OK;
 }
 
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
@@ -837,8 +901,11 @@ kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launch
   return KSTAP_OK;
 }
 
+void server_shutdown(kstap_ctx* ctx);
+
 kstap_status kstap_destroy(kstap_ctx* ctx) {
   if (!ctx) return KSTAP_EINVAL;
+  server_shutdown(ctx);
   if (ctx->ws || ctx->bank_aT || ctx->jobs_dev) cudaStreamSynchronize(ctx->stream);
   for (int k = 0; k <= kstap_nkernels; ++k)
     if (ctx->ev[k][0]) {
@@ -856,6 +923,411 @@ kstap_status kstap_destroy(kstap_ctx* ctx) {
 
 const char* kstap_last_error(const kstap_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: kstap_submit / kstap_poll / kstap_release.
+//
+// One worker thread per context admits pending requests in arrival order
+// while their device memory fits the context's HBM budget, groups whatever is
+// admissible into one batch (up to max_batch frames, same kernels as
+// kstap_run_batch) and enqueues it on one of several streams, so that batches
+// overlap on the device and requests arriving meanwhile join the next batch
+// (continuous batching).  Scratch (workspace, factors, the device copy of a
+// host frame, the job table) is allocated stream-ordered and freed right after
+// the batch's kernels; results stay on the device until kstap_release.  A
+// host callback on the stream stamps completion and returns the budget.
+// ---------------------------------------------------------------------------
+struct Server {
+  struct Part {                     // one row strip of a request (or the whole frame)
+    Frame fr;                       // Y view, outputs offset; factors filled at launch
+    size_t scratch_bytes = 0;
+    int state = 0;                  // 0 pending, 1 running, 2 done
+  };
+  struct Req {
+    bool on_host = false;
+    int H_in = 0, W_in = 0, H = 0, W = 0;
+    int state = 0;                  // 0 pending, 1 running, 2 done, 3 error
+    int remaining = 0;              // parts not yet done
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t out_bytes = 0;
+    float* Tmax = nullptr;
+    int32_t* vidx = nullptr;
+    uint8_t* map = nullptr;
+    void* out_mem = nullptr;
+    std::vector<Part> parts;
+  };
+  struct Batch {
+    Server* srv;
+    std::vector<std::pair<uint64_t, int>> items;   // (ticket, part)
+    size_t scratch_bytes = 0;
+  };
+  kstap_ctx* ctx = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::pair<uint64_t, int>> pending;      // (ticket, part) in arrival order
+  std::unordered_map<uint64_t, Req> reqs;
+  std::thread worker;
+  bool stop = false;
+  size_t used = 0;
+  int inflight = 0;
+  int max_batch = 16;
+  int max_inflight = 4;
+  uint64_t next_ticket = 1;
+  std::vector<cudaStream_t> streams;
+  int rr = 0;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  std::string err;
+
+  double now_us() const {
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0)
+        .count();
+  }
+};
+
+namespace {
+
+size_t factor_bytes(const kstap_params& p, size_t cells) {
+  return cells * ((size_t)p.p * p.r_a * 8 + 2 * (size_t)p.q * p.r_b * 8 + (size_t)p.r_a * 4 +
+                  (size_t)p.r_b * 4 + 4 + 4);
+}
+
+void CUDART_CB batch_done(void* arg) {
+  Server::Batch* b = (Server::Batch*)arg;
+  Server* s = b->srv;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    const double t = s->now_us();
+    for (auto& it : b->items) {
+      auto r = s->reqs.find(it.first);
+      if (r == s->reqs.end()) continue;
+      Server::Part& pt = r->second.parts[it.second];
+      if (pt.state == 1) {
+        pt.state = 2;
+        if (--r->second.remaining == 0 && r->second.state == 1) {
+          r->second.state = 2;
+          r->second.t_done = t;
+        }
+      }
+    }
+    s->used -= b->scratch_bytes;
+    s->inflight -= 1;
+  }
+  s->cv.notify_all();
+  delete b;
+}
+
+// Enqueues one admitted batch (called by the worker without the lock held).
+void launch_batch(Server* s, const std::vector<std::pair<uint64_t, int>>& items) {
+  kstap_ctx* ctx = s->ctx;
+  const kstap_params& p = ctx->prm;
+  cudaStream_t st = s->streams[s->rr++ % s->streams.size()];
+  std::vector<Frame> fr;
+  std::vector<bool> host;
+  Server::Batch* b = new Server::Batch{s, items, 0};
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto& it : items) {
+      const Server::Req& r = s->reqs[it.first];
+      fr.push_back(r.parts[it.second].fr);
+      host.push_back(r.on_host);
+      b->scratch_bytes += r.parts[it.second].scratch_bytes;
+    }
+  }
+  std::vector<std::pair<int, int>> HW;
+  size_t fbytes = 0, ybytes = 0;
+  for (size_t k = 0; k < fr.size(); ++k) {
+    const int H = fr[k].H_in - 2 * p.ring_r, W = fr[k].W_in - 2 * p.ring_a - p.q + 1;
+    HW.push_back({H, W});
+    fbytes += up256(factor_bytes(p, (size_t)H * W));
+    if (host[k]) ybytes += up256((size_t)p.p * fr[k].H_in * fr[k].W_in * sizeof(kstap_c64));
+  }
+  const Layout L = make_layout(p, HW, true);
+  const size_t total = up256(L.total) + fbytes + ybytes + up256(fr.size() * sizeof(Job));
+  char* mem = nullptr;
+  kstap_status status = KSTAP_OK;
+  if (cudaMallocAsync((void**)&mem, total, st) != cudaSuccess) {
+    status = KSTAP_ENOMEM;
+  } else {
+    char* ws = mem;
+    char* fac = mem + up256(L.total);
+    char* yc = fac + fbytes;
+    Job* jt = (Job*)(yc + ybytes);
+    for (size_t k = 0; k < fr.size(); ++k) {
+      const size_t cells = (size_t)HW[k].first * HW[k].second;
+      char* q = fac;
+      kstap_factors& f = fr[k].f;
+      f.UA = (kstap_c64*)q;
+      q += cells * p.p * p.r_a * 8;
+      f.UB_hi = (kstap_c64*)q;
+      q += cells * p.q * p.r_b * 8;
+      f.UB_lo = (kstap_c64*)q;
+      q += cells * p.q * p.r_b * 8;
+      f.lamA = (float*)q;
+      q += cells * p.r_a * 4;
+      f.lamB = (float*)q;
+      q += cells * p.r_b * 4;
+      f.iters = (int32_t*)q;
+      q += cells * 4;
+      f.eta = (float*)q;
+      fac += up256(factor_bytes(p, cells));
+      if (host[k]) {
+        // host frame: copy this part's rows of every channel to a dense device block
+        const long long cs = fr[k].ch_stride ? fr[k].ch_stride
+                                             : (long long)fr[k].H_in * fr[k].W_in;
+        const size_t plane = (size_t)fr[k].H_in * fr[k].W_in;
+        for (int i = 0; i < p.p; ++i)
+          cudaMemcpyAsync(yc + i * plane * sizeof(kstap_c64), fr[k].Y + (size_t)i * cs,
+                          plane * sizeof(kstap_c64), cudaMemcpyHostToDevice, st);
+        fr[k].Y = (const kstap_c64*)yc;
+        fr[k].ch_stride = (long long)plane;
+        yc += up256(p.p * plane * sizeof(kstap_c64));
+      }
+    }
+    if (fr.size() > 1) {
+      const Geom g = make_geom(p, ctx->V, ctx->tune.tc);
+      std::vector<Job> hj;
+      JobList JL;
+      fill_jobs(p, g, fr, ws, &L, hj, JL);
+      cudaMemcpyAsync(jt, hj.data(), hj.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
+    }
+    status = enqueue_batch(ctx, nullptr, fr, L, ws, jt, st);
+    cudaFreeAsync(mem, st);
+  }
+  if (status != KSTAP_OK) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto& it : items) s->reqs[it.first].state = 3;
+    s->err = ctx->err;
+  }
+  if (cudaLaunchHostFunc(st, batch_done, b) != cudaSuccess) {
+    // could not register the completion callback: finish synchronously
+    cudaStreamSynchronize(st);
+    batch_done(b);
+  }
+}
+
+void worker_loop(Server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto part_bytes = [&](const std::pair<uint64_t, int>& it) {
+    return s->reqs[it.first].parts[it.second].scratch_bytes;
+  };
+  while (true) {
+    s->cv.wait(lock, [&] {
+      if (s->stop) return true;
+      if (s->pending.empty() || s->inflight >= s->max_inflight) return false;
+      return !s->ctx->budget || s->used + part_bytes(s->pending.front()) <= s->ctx->budget ||
+             s->inflight == 0;
+    });
+    if (s->stop) break;
+    std::vector<std::pair<uint64_t, int>> batch;
+    while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
+      const auto it = s->pending.front();
+      const size_t need = part_bytes(it);
+      if (s->ctx->budget && s->used + need > s->ctx->budget && !(batch.empty() && s->inflight == 0))
+        break;
+      s->used += need;
+      Server::Req& r = s->reqs[it.first];
+      r.parts[it.second].state = 1;
+      if (r.state == 0) {
+        r.state = 1;
+        r.t_admit = s->now_us();
+      }
+      batch.push_back(it);
+      s->pending.pop_front();
+    }
+    if (batch.empty()) continue;
+    s->inflight += 1;
+    lock.unlock();
+    launch_batch(s, batch);
+    lock.lock();
+  }
+}
+
+Server* get_server(kstap_ctx* ctx) {
+  if (ctx->server) return ctx->server;
+  Server* s = new Server();
+  s->ctx = ctx;
+  cudaGetDevice(&s->device);
+  // keep freed stream-ordered allocations in the pool between batches
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  for (int k = 0; k < s->max_inflight; ++k) {
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    s->streams.push_back(st);
+  }
+  s->worker = std::thread(worker_loop, s);
+  ctx->server = s;
+  return s;
+}
+
+}  // namespace
+
+void server_shutdown(kstap_ctx* ctx) {
+  Server* s = ctx->server;
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto st : s->streams) cudaStreamSynchronize(st);
+  for (auto& kv : s->reqs)
+    if (kv.second.out_mem) cudaFree(kv.second.out_mem);
+  for (auto st : s->streams) cudaStreamDestroy(st);
+  delete s;
+  ctx->server = nullptr;
+}
+
+extern "C" {
+
+kstap_status kstap_serve_config(kstap_ctx* ctx, int max_batch, int max_inflight) {
+  if (!ctx) return KSTAP_EINVAL;
+  if (ctx->server) return fail(ctx, KSTAP_EINVAL, "configure serving before the first submit");
+  if (max_batch < 1 || max_batch > 1024 || max_inflight < 1 || max_inflight > 16)
+    return fail(ctx, KSTAP_EINVAL, "max_batch in [1, 1024], max_inflight in [1, 16]");
+  Server* s = get_server(ctx);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->max_batch = max_batch;
+  }
+  // rebuild the stream pool for the new in-flight limit
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  s->worker.join();
+  for (auto st : s->streams) cudaStreamDestroy(st);
+  s->streams.clear();
+  s->stop = false;
+  s->max_inflight = max_inflight;
+  for (int k = 0; k < max_inflight; ++k) {
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    s->streams.push_back(st);
+  }
+  s->worker = std::thread(worker_loop, s);
+  return KSTAP_OK;
+}
+
+kstap_status kstap_submit(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in, int flags,
+                          uint64_t* ticket) {
+  if (!ticket) return fail(ctx, KSTAP_EINVAL, "ticket is NULL");
+  kstap_status st = check_frame(ctx, Y, H_in, W_in);
+  if (st != KSTAP_OK) return st;
+  const kstap_params& p = ctx->prm;
+  Server::Req r;
+  r.on_host = (flags & KSTAP_FRAME_ON_HOST) != 0;
+  r.H_in = H_in;
+  r.W_in = W_in;
+  r.H = H_in - 2 * p.ring_r;
+  r.W = W_in - 2 * p.ring_a - p.q + 1;
+  const size_t cells = (size_t)r.H * r.W;
+  r.out_bytes = up256(cells * 4) * 2 + up256(cells);
+  auto part_scratch = [&](int rows) {
+    return make_layout(p, {{rows, r.W}}, true).total + factor_bytes(p, (size_t)rows * r.W) +
+           (r.on_host ? (size_t)p.p * (rows + 2 * p.ring_r) * W_in * sizeof(kstap_c64) : 0) +
+           4096;
+  };
+  // frames whose scratch exceeds a quarter of the budget are served as row
+  // strips admitted one by one (at least kMomRows rows each)
+  int rows = r.H;
+  if (ctx->budget && part_scratch(r.H) > ctx->budget / 4) {
+    const size_t per_row = std::max<size_t>(1, part_scratch(1));
+    rows = (int)std::max<size_t>(kstap::kMomRows, (ctx->budget / 4) / per_row);
+    rows -= rows % kstap::kMomRows;
+  }
+  if (ctx->budget && part_scratch(std::min(rows, r.H)) + r.out_bytes > ctx->budget)
+    return fail(ctx, KSTAP_ENOMEM, "frame needs %zu B per strip, more than the HBM budget %zu B",
+                part_scratch(std::min(rows, r.H)) + r.out_bytes, ctx->budget);
+  cudaError_t e = cudaMalloc(&r.out_mem, r.out_bytes);   // results, held until kstap_release
+  if (e != cudaSuccess)
+    return fail(ctx, KSTAP_ENOMEM, "result cudaMalloc(%zu): %s", r.out_bytes,
+                cudaGetErrorString(e));
+  r.Tmax = (float*)r.out_mem;
+  r.vidx = (int32_t*)((char*)r.out_mem + up256(cells * 4));
+  r.map = (uint8_t*)((char*)r.out_mem + 2 * up256(cells * 4));
+  const Frame whole{Y, H_in, W_in, kstap_factors{}, r.Tmax, r.vidx, r.map, nullptr};
+  const std::vector<Frame> strips =
+      rows >= r.H ? std::vector<Frame>{whole} : split_rows(p, ctx->V, whole, rows);
+  for (const Frame& f : strips) {
+    Server::Part pt;
+    pt.fr = f;
+    pt.scratch_bytes = part_scratch(f.H_in - 2 * p.ring_r);
+    r.parts.push_back(pt);
+  }
+  r.remaining = (int)r.parts.size();
+  Server* s = get_server(ctx);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->used += r.out_bytes;   // results count against the budget until released
+    r.t_submit = s->now_us();
+    const uint64_t tk = s->next_ticket++;
+    const int np = (int)r.parts.size();
+    s->reqs[tk] = std::move(r);
+    for (int k = 0; k < np; ++k) s->pending.push_back({tk, k});
+    *ticket = tk;
+  }
+  s->cv.notify_all();
+  return KSTAP_OK;
+}
+
+kstap_status kstap_poll(kstap_ctx* ctx, uint64_t ticket, kstap_result* out, int timeout_us) {
+  if (!ctx || !out) return KSTAP_EINVAL;
+  Server* s = ctx->server;
+  if (!s) return fail(ctx, KSTAP_ENOTFOUND, "no request was submitted");
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return fail(ctx, KSTAP_ENOTFOUND, "unknown ticket %llu",
+                                       (unsigned long long)ticket);
+  auto ready = [&] { return s->reqs[ticket].state >= 2; };
+  if (!ready()) {
+    if (timeout_us == 0) return KSTAP_EAGAIN;
+    if (timeout_us < 0)
+      s->cv.wait(lock, ready);
+    else if (!s->cv.wait_for(lock, std::chrono::microseconds(timeout_us), ready))
+      return KSTAP_ETIMEOUT;
+  }
+  const Server::Req& r = s->reqs[ticket];
+  if (r.state == 3) return fail(ctx, KSTAP_ECUDA, "request failed: %s", s->err.c_str());
+  out->ticket = ticket;
+  out->H = r.H;
+  out->W = r.W;
+  out->Tmax = r.Tmax;
+  out->vidx = r.vidx;
+  out->map = r.map;
+  out->t_submit_us = r.t_submit;
+  out->t_admit_us = r.t_admit;
+  out->t_done_us = r.t_done;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket) {
+  if (!ctx || !ctx->server) return KSTAP_EINVAL;
+  Server* s = ctx->server;
+  void* mem = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+      return fail(ctx, KSTAP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (it->second.state < 2) return fail(ctx, KSTAP_EAGAIN, "request still in flight");
+    mem = it->second.out_mem;
+    s->used -= it->second.out_bytes;
+    s->reqs.erase(it);
+  }
+  s->cv.notify_all();
+  if (mem) cudaFree(mem);
+  return KSTAP_OK;
 }
 
 }  // extern "C"

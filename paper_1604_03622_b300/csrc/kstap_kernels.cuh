@@ -52,6 +52,7 @@ struct Geom {
   float eps;
   float tau;
   int tc;         // cells per tile in the B pass
+  long long ch_stride;   // elements between channel planes of Y (>= H_in * W_in)
 };
 
 // One frame of a batch.  Per-cell workspace arrays of a launch are
@@ -59,8 +60,9 @@ struct Geom {
 // starting at cell0; its lag store starts at lag0 (float4 units).
 enum { kKindMoments = 0, kKindFlip = 1, kKindBfit = 2, kKindDetect = 3 };
 struct Job {
-  const float2* Y;
-  int H_in, W_in, H, W;
+  const float2* Y;              // first row of this job's rows, channel 0
+  int H_in, W_in, H, W;         // rows / columns of this job (a frame or a row strip of one)
+  long long ch_stride;          // elements between channel planes
   long long cell0, lag0;
   unsigned* maxbits;            // 2 words: max |component| bits, non-finite flag
   float2* UA;
@@ -108,6 +110,7 @@ __device__ __forceinline__ Geom with_job(const Geom& g0, const Job& J) {
   Geom g = g0;
   g.H_in = J.H_in;
   g.W_in = J.W_in;
+  g.ch_stride = J.ch_stride;
   g.H = J.H;
   g.W = J.W;
   return g;
@@ -160,13 +163,15 @@ __host__ __device__ constexpr int tri_idx(int n, int J, int Jp) {
 __global__ void k_frame_maxabs(Geom g0, JobList L) {
   const Job& J = L.table ? L.table[blockIdx.y] : L.one;
   const float* __restrict__ Y = reinterpret_cast<const float*>(J.Y);
-  const size_t nfloat = 2 * (size_t)g0.p * J.H_in * J.W_in;
+  const size_t plane = 2 * (size_t)J.H_in * J.W_in;   // floats of one channel of this job
+  const size_t nfloat = plane * g0.p;
   unsigned* maxbits = J.maxbits;
   unsigned* nonfinite = J.maxbits + 1;
   unsigned m = 0, bad = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nfloat;
        i += (size_t)gridDim.x * blockDim.x) {
-    const float a = fabsf(__ldg(Y + i));
+    const size_t ch = i / plane;
+    const float a = fabsf(__ldg(Y + ch * 2 * (size_t)J.ch_stride + (i - ch * plane)));
     if (a < 3.4e38f) {
       m = max(m, __float_as_uint(a));
     } else {
@@ -199,7 +204,7 @@ __device__ void load_tile_q(const float2* __restrict__ Y, const Geom& g, int r, 
     const int gc = c0 + col;
     int2 v = make_int2(0, 0);
     if (gc < g.W_in) {
-      const float2 y = __ldg(Y + ((size_t)i * g.H_in + (r + rho)) * g.W_in + gc);
+      const float2 y = __ldg(Y + (size_t)i * g.ch_stride + (size_t)(r + rho) * g.W_in + gc);
       v.x = quantise(y.x, scale);
       v.y = quantise(y.y, scale);
     }
@@ -323,7 +328,7 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
       const int gr = r0 + rho, gc = c0 + col;
       int2 v = make_int2(0, 0);
       if (gc < g.W_in && gr < g.H_in) {
-        const float2 y = __ldg(Y + ((size_t)i * g.H_in + gr) * g.W_in + gc);
+        const float2 y = __ldg(Y + (size_t)i * g.ch_stride + (size_t)gr * g.W_in + gc);
         v.x = quantise(y.x, scale);
         v.y = quantise(y.y, scale);
       }
@@ -1090,7 +1095,8 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
     const int r = (int)(cell / g.W), c = (int)(cell % g.W);
 #pragma unroll
     for (int i = 0; i < P; ++i)
-      Xs[i * Q + gl] = __ldg(Y + ((size_t)i * g.H_in + (r + g.Rr)) * g.W_in + (c + g.Ra + gl));
+      Xs[i * Q + gl] =
+          __ldg(Y + (size_t)i * g.ch_stride + (size_t)(r + g.Rr) * g.W_in + (c + g.Ra + gl));
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       Uh[gl * R + m] = UBh[(cell * Q + gl) * R + m];
