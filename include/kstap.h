@@ -49,6 +49,7 @@ typedef struct {
 } kstap_c64; /* interleaved complex64 */
 
 typedef enum {
+  KSTAP_WARN_NOCONV = 1, /* kstap_fit_report: some cells stopped at max_iter (results valid) */
   KSTAP_OK = 0,
   KSTAP_EINVAL = -1,   /* bad argument; nothing was enqueued */
   KSTAP_ENOMEM = -2,   /* workspace would exceed the HBM budget, or cudaMalloc failed */
@@ -112,16 +113,30 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
 /* Steps 1-2 above (Eq. SCM, Alg. 1 as an index map, Alg. 2, EIG_{r_b} of
  * B^): fits every cell of the frame Y (device, p x H_in x W_in complex64)
  * and writes the factors.  Requires H_in >= 2 ring_r + 1 and
- * W_in >= 2 ring_a + q.  Grows the workspace when needed
- * (KSTAP_ENOMEM if over budget). */
+ * W_in >= 2 ring_a + q.  Grows the workspace when needed; a frame whose
+ * workspace exceeds the budget runs as row strips (KSTAP_ENOMEM if even a
+ * 4-row strip does not fit).  The call is asynchronous on the context stream.
+ * Non-finite input: NaN / Inf samples enter the sums as 0, and every cell
+ * whose box (rows r .. r + 2 ring_r, columns c .. c + 2 ring_a + q - 1 of
+ * every channel, i.e. its training windows, guard and test window) holds one
+ * gets iters = -1 and eta = NaN; its factors are not meaningful. */
 kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
                                const kstap_factors* factors);
+
+/* Waits for the context stream, then reports the last kstap_fit_project or
+ * kstap_run_batch: cells whose Alg. 2 loop stopped at max_iter and cells
+ * flagged for non-finite input (either pointer may be NULL).  Returns
+ * KSTAP_WARN_NOCONV if any cell stopped at max_iter (its factors are the last
+ * iterate, valid but not converged to eps), else KSTAP_OK. */
+kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite);
 
 /* Steps 3-4 above (Eq. KronSTAP and the velocity bank) with the factors of a
  * previous kstap_fit_project on the same frame.  Outputs (device, H * W):
  * Tmax float, vidx int32 (lowest maximising v), map uint8 (Tmax > tau);
  * T_all (device, [k][V] float) may be NULL.  Velocities whose steering
- * vector keeps less than 1e-12 of its energy after projection get T_v = 0. */
+ * vector keeps less than 1e-12 of its energy after projection get T_v = 0.
+ * Cells whose box (see kstap_fit_project) holds a NaN / Inf sample of this Y
+ * get Tmax = NaN, vidx = -1, map = 0 and T_all = NaN. */
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
                           const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
                           float* T_all);

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkstap.so")
 
 KSTAP_OK = 0
-STATUS = {0: "KSTAP_OK", -1: "KSTAP_EINVAL", -2: "KSTAP_ENOMEM", -3: "KSTAP_ECUDA",
+KSTAP_WARN_NOCONV = 1
+STATUS = {1: "KSTAP_WARN_NOCONV", 0: "KSTAP_OK", -1: "KSTAP_EINVAL", -2: "KSTAP_ENOMEM", -3: "KSTAP_ECUDA",
           -4: "KSTAP_EAGAIN", -5: "KSTAP_ETIMEOUT", -6: "KSTAP_ENOTFOUND"}
 
 EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
@@ -23,7 +24,7 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
-            "kstap_release"]
+            "kstap_release", "kstap_fit_report"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -101,13 +102,16 @@ def lib() -> ctypes.CDLL:
         L.kstap_submit.argtypes = [P, P, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
         L.kstap_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KstapResult), I]
         L.kstap_release.argtypes = [P, ctypes.c_uint64]
+        L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong)]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
         for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
                      "kstap_set_profiling", "kstap_kernel_times", "kstap_fit_project_noalloc",
                      "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
-                     "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release"):
+                     "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
+                     "kstap_fit_report"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -145,6 +149,16 @@ def make_factors(UA, UB_hi, UB_lo, lamA=None, lamB=None, iters=None, eta=None) -
 
 def kstap_fit_project(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors) -> None:
     _check(lib().kstap_fit_project(ctx, _ptr(Y), H_in, W_in, ctypes.byref(factors)), ctx)
+
+
+def kstap_fit_report(ctx: int):
+    """(nonconverged, nonfinite) cell counts of the last fit; waits for the stream.
+    A KSTAP_WARN_NOCONV status is returned in the counts, not raised."""
+    nc, nf = ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib().kstap_fit_report(ctx, ctypes.byref(nc), ctypes.byref(nf))
+    if st != KSTAP_WARN_NOCONV:
+        _check(st, ctx)
+    return int(nc.value), int(nf.value)
 
 
 def kstap_detect(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors, Tmax, vidx, map_,

@@ -60,6 +60,10 @@ struct kstap_ctx {
   int kernel_launches[kstap_nkernels] = {};
   bool ev_pending[kstap_nkernels] = {};
   struct Server* server = nullptr;   // created by the first kstap_submit
+  // device words: frame scan of kstap_detect (max bits, non-finite flag) and
+  // the counters of the last fit ([0] cells at max_iter, [1] non-finite cells)
+  unsigned* det_flags = nullptr;
+  unsigned long long* report = nullptr;
 };
 
 struct kstap_graph {
@@ -374,6 +378,21 @@ int grid_for(K kernel, int threads, size_t smem, int tiles, int sm_count, int wa
   return (int)std::max(1L, std::min<long>(tiles, cap));
 }
 
+// Frame scan of every job: max |component| (fixed-point scale) and the
+// non-finite flag, into each job's maxbits words (zeroed by the caller).
+kstap_status enqueue_scan(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                          int sm_count, cudaStream_t s) {
+  const size_t maxf = JL.table ? 0 : 2 * (size_t)g.p * JL.one.H_in * JL.one.W_in;
+  const int bx = JL.table ? sm_count * 2
+                          : (int)std::min<size_t>((maxf + 1023) / 1024, (size_t)sm_count * 16);
+  prof_collect(prof, KSTAP_K_SCALE);
+  prof_begin(prof, KSTAP_K_SCALE, s);
+  kstap::k_frame_maxabs<<<dim3(std::max(1, bx), JL.njobs), 256, 0, s>>>(g, JL);
+  prof_end(prof, KSTAP_K_SCALE, s);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+  return KSTAP_OK;
+}
+
 // Enqueues the fit (scale, moments, flip-flop, B / U_B) of all jobs of JL.
 template <int P, int Q, int R>
 kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
@@ -385,14 +404,8 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
   float4* Lw = lag_store ? (float4*)(scratch + L.Lw) : nullptr;
   if (JL.njobs < 1) return KSTAP_OK;
   KSTAP_CUDA(ctx, cudaMemsetAsync(scratch + L.flags, 0, 8 * (size_t)JL.njobs, s));
-  const size_t maxf = JL.table ? 0 : 2 * (size_t)P * JL.one.H_in * JL.one.W_in;
-  const int bx = JL.table ? sm_count * 2
-                          : (int)std::min<size_t>((maxf + 1023) / 1024, (size_t)sm_count * 16);
-  prof_collect(prof, KSTAP_K_SCALE);
-  prof_begin(prof, KSTAP_K_SCALE, s);
-  kstap::k_frame_maxabs<<<dim3(std::max(1, bx), JL.njobs), 256, 0, s>>>(g, JL);
-  prof_end(prof, KSTAP_K_SCALE, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
+  kstap_status st = enqueue_scan(ctx, prof, g, JL, sm_count, s);
+  if (st != KSTAP_OK) return st;
 
   const size_t sm1 = smem_moments(g);
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_moments<P, Q>,
@@ -534,12 +547,13 @@ kstap_status frames_from(kstap_ctx* ctx, const kstap_frame* frames, int n,
 // device job table (unused for a single frame, whose job goes by value).
 kstap_status enqueue_batch(kstap_ctx* ctx, kstap_ctx* prof, const std::vector<Frame>& fr,
                            const Layout& L, char* scratch, const Job* jobs_dev,
-                           cudaStream_t s) {
+                           cudaStream_t s, unsigned long long* report = nullptr) {
   const Geom g = make_geom(ctx->prm, ctx->V, ctx->tune.tc);
   std::vector<Job> host;
   JobList JL;
   fill_jobs(ctx->prm, g, fr, scratch, &L, host, JL);
   if (fr.size() > 1) JL.table = jobs_dev;
+  JL.report = report;
   kstap_status st = dispatch_fit(ctx, prof, g, JL, scratch, L, true, ctx->sm_count,
                                  ctx->tune.waves, s);
   if (st != KSTAP_OK) return st;
@@ -602,7 +616,12 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
     n2[v] = (float)sa;
     n2[V + v] = (float)sb;
   }
-  e = cudaMalloc(&ctx->bank_aT, aT.size() * sizeof(float2));
+  e = cudaMalloc(&ctx->report, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    ctx->det_flags = (unsigned*)(ctx->report + 2);
+    e = cudaMemset(ctx->report, 0, 4 * sizeof(unsigned long long));
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_aT, aT.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_bT, bT.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_n2, n2.size() * sizeof(float));
   if (e == cudaSuccess)
@@ -643,6 +662,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
   }
   const std::vector<Frame> strips = (rows >= H) ? std::vector<Frame>{whole}
                                                 : split_rows(p, ctx->V, whole, rows);
+  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, 2 * sizeof(unsigned long long), ctx->stream));
   for (const Frame& s : strips) {
     const int sh = s.H_in - 2 * p.ring_r;
     const Layout L = make_layout(p, {{sh, W}}, true);
@@ -652,6 +672,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
     std::vector<Job> jobs;
     JobList JL;
     fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
+    JL.report = ctx->report;
     st = dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
                       ctx->stream);
     if (st != KSTAP_OK) return st;
@@ -672,6 +693,11 @@ kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
   std::vector<Job> jobs;
   JobList JL;
   fill_jobs(ctx->prm, g, fr, nullptr, nullptr, jobs, JL);
+  // this frame's own scan, for the per-cell non-finite flags
+  JL.one.maxbits = ctx->det_flags;
+  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->det_flags, 0, 2 * sizeof(unsigned), ctx->stream));
+  st = enqueue_scan(ctx, ctx, g, JL, ctx->sm_count, ctx->stream);
+  if (st != KSTAP_OK) return st;
   return dispatch_detect(ctx, ctx, g, JL, ctx->sm_count, ctx->tune.waves, ctx->stream);
 }
 
@@ -705,7 +731,18 @@ kstap_status kstap_run_batch(kstap_ctx* ctx, const kstap_frame* frames, int n) {
     KSTAP_CUDA(ctx, cudaMemcpyAsync(ctx->jobs_dev, host.data(), n * sizeof(Job),
                                     cudaMemcpyHostToDevice, ctx->stream));
   }
-  return enqueue_batch(ctx, ctx, fr, L, (char*)ctx->ws, ctx->jobs_dev, ctx->stream);
+  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  return enqueue_batch(ctx, ctx, fr, L, (char*)ctx->ws, ctx->jobs_dev, ctx->stream, ctx->report);
+}
+
+kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite) {
+  if (!ctx) return KSTAP_EINVAL;
+  unsigned long long h[2] = {0, 0};
+  KSTAP_CUDA(ctx, cudaMemcpyAsync(h, ctx->report, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (nonconverged) *nonconverged = (long long)h[0];
+  if (nonfinite) *nonfinite = (long long)h[1];
+  return h[0] ? KSTAP_WARN_NOCONV : KSTAP_OK;
 }
 
 kstap_status kstap_graph_create(kstap_ctx* const* ctxs, const kstap_frame* const* frames,
@@ -906,7 +943,8 @@ void server_shutdown(kstap_ctx* ctx);
 kstap_status kstap_destroy(kstap_ctx* ctx) {
   if (!ctx) return KSTAP_EINVAL;
   server_shutdown(ctx);
-  if (ctx->ws || ctx->bank_aT || ctx->jobs_dev) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws || ctx->bank_aT || ctx->jobs_dev || ctx->report)
+    cudaStreamSynchronize(ctx->stream);
   for (int k = 0; k <= kstap_nkernels; ++k)
     if (ctx->ev[k][0]) {
       cudaEventDestroy(ctx->ev[k][0]);
@@ -917,6 +955,7 @@ kstap_status kstap_destroy(kstap_ctx* ctx) {
   cudaFree(ctx->bank_aT);
   cudaFree(ctx->bank_bT);
   cudaFree(ctx->bank_n2);
+  cudaFree(ctx->report);
   delete ctx;
   return KSTAP_OK;
 }

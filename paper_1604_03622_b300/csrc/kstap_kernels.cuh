@@ -87,6 +87,7 @@ struct JobList {
   int njobs;
   int ntiles[4];
   long long NC;                 // total cells (stride of the per-cell workspace arrays)
+  unsigned long long* report;   // optional counters: [0] cells at max_iter, [1] cells flagged non-finite
 };
 
 __device__ __forceinline__ const Job& job_of(const JobList& L, int kind, int tile, int& local) {
@@ -139,11 +140,39 @@ __device__ __forceinline__ float2 warp_sum2(float2 v) {
   return make_float2(warp_sum(v.x), warp_sum(v.y));
 }
 
+constexpr float kFltMax = 3.4028234663852886e38f;
+
 // Frame fixed-point shift: maxabs * 2^sh < 2^B.
 __device__ __forceinline__ int frame_shift(unsigned maxbits, int B) {
   const float m = __uint_as_float(maxbits);
-  if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+  if (!(m > 0.f) || !(m <= kFltMax)) return 0;
   return B - 1 - ilogbf(m);
+}
+
+// True if any sample of cell (r, c)'s box is NaN or infinite: rows
+// [r, r + 2 Rr] and columns [c, c + 2 Ra + q - 1] of every channel (the union
+// of its training windows, its guard and its test window).  Lanes `lane` of
+// `nl` share the scan; the caller combines their answers.  Only run when the
+// frame scan found a non-finite value, so the finite path never pays for it.
+__device__ __forceinline__ bool box_nonfinite(const float2* __restrict__ Y, const Geom& g, int r,
+                                              int c, int lane, int nl) {
+  const int NR = 2 * g.Rr + 1, NK = 2 * g.Ra + g.q;
+  const int tot = g.p * NR * NK;
+  bool bad = false;
+  for (int idx = lane; idx < tot; idx += nl) {
+    const int kap = idx % NK, rho = (idx / NK) % NR, i = idx / (NK * NR);
+    const float2 y = __ldg(Y + (size_t)i * g.ch_stride + (size_t)(r + rho) * g.W_in + c + kap);
+    bad |= !(fabsf(y.x) <= kFltMax) || !(fabsf(y.y) <= kFltMax);
+  }
+  return bad;
+}
+
+// Adds the number of lanes of the calling (converged) warp subset with
+// `flag` set to *ctr: one atomic per warp.
+__device__ __forceinline__ void count_lanes(unsigned long long* ctr, bool flag) {
+  const unsigned mask = __activemask();
+  const unsigned b = __ballot_sync(mask, flag);
+  if (b && (threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(ctr, (unsigned long long)__popc(b));
 }
 
 __device__ __forceinline__ int quantise(float y, float scale) {
@@ -172,7 +201,7 @@ __global__ void k_frame_maxabs(Geom g0, JobList L) {
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t ch = i / plane;
     const float a = fabsf(__ldg(Y + ch * 2 * (size_t)J.ch_stride + (i - ch * plane)));
-    if (a < 3.4e38f) {
+    if (a <= kFltMax) {
       m = max(m, __float_as_uint(a));
     } else {
       bad = 1;
@@ -667,7 +696,16 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
     }
     if (dn <= tol2 * nn) break;
   }
-  if (it > g.max_iter) it = g.max_iter;
+  const bool noconv = it > g.max_iter;
+  if (noconv) it = g.max_iter;
+  if (JL.report) count_lanes(JL.report, noconv);
+  // cells whose box holds a NaN / Inf sample: iters = -1, eta = NaN
+  bool bad = false;
+  if (JB.maxbits && JB.maxbits[1]) {
+    Geom gj = with_job(g0, JB);
+    bad = box_nonfinite(JB.Y, gj, (int)(local / JB.W), (int)(local % JB.W), 0, 1);
+    if (JL.report) count_lanes(JL.report + 1, bad);
+  }
   // eta^2 = 1 - a^H M a / (|a|^2 tr M) for b matched to the final a
   double tr = 0.0, aMa = 0.0, an = 0.0;
 #pragma unroll
@@ -700,10 +738,10 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
     for (int m = 0; m < P; ++m)
       if (m < ra) lamA[local * ra + m] = d[m] * sc;
   }
-  if (iters) iters[local] = it;
+  if (iters) iters[local] = bad ? -1 : it;
   if (eta) {
     double e2 = (tr > 0.0 && an > 0.0) ? 1.0 - aMa / (an * tr) : 0.0;
-    eta[local] = (float)sqrt(e2 > 0.0 ? e2 : 0.0);
+    eta[local] = bad ? __int_as_float(0x7fc00000) : (float)sqrt(e2 > 0.0 ? e2 : 0.0);
   }
   }  // tile loop
 }
@@ -861,7 +899,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
         cff t = cff{Gm[m][i].re, ff_neg(Gm[m][i].im)};
 #pragma unroll
         for (int k = 0; k < m; ++k) t = cff_sub(t, cff_mul(L[i][k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
-        L[i][m] = cff{ff_div(t.re, lmm), ff_div(t.im, lmm)};
+        L[i][m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
       }
     }
     // U = Y L^-H (row j)
@@ -1274,6 +1312,19 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
     if (ob > best || (ob == best && ov < bestv)) {
       best = ob;
       bestv = ov;
+    }
+  }
+  // cells whose box holds a NaN / Inf sample: Tmax = NaN, vidx = -1, map = 0
+  // (the frame flag is per job, so the branch is uniform over the warp)
+  if (JB.maxbits && JB.maxbits[1]) {
+    bool bad = live && box_nonfinite(Y, g, (int)(cell / g.W), (int)(cell % g.W), gl, G);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    if (bad) {
+      best = __int_as_float(0x7fc00000);
+      bestv = -1;
+      if (T_all)
+        for (int v = gl; v < V; v += G) T_all[cell * V + v] = best;
     }
   }
   if (live && gl == 0) {
