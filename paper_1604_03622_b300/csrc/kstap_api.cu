@@ -352,9 +352,11 @@ size_t smem_bfit(const Geom& g, bool from_store) {
   const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
   size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
   b += (size_t)TC * PP * 8;
-  // the eigen phase's basis scratch reuses the (then dead) lag and box-sum buffers
-  const size_t vs = (size_t)(kstap::kThreads / 32) * (32 / Q) * Q * R * 8;
-  const size_t lagb = (size_t)PP * NUmax * 16 + (from_store ? 0 : 2 * (size_t)PP * WT * 16);
+  // the eigen phase's basis scratch reuses the (then dead) lag and box-sum
+  // buffers; the lag store is read through two buffers (prefetch of the next lag)
+  const size_t vs = (size_t)(kstap::bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;
+  const size_t lagb = (from_store ? kstap::kLagStages : 1) * (size_t)PP * NUmax * 16 +
+                      (from_store ? 0 : 2 * (size_t)PP * WT * 16);
   b += std::max(vs, lagb);
   if (!from_store) b += (size_t)P * NR * WT * 8;
   return b;
@@ -429,10 +431,11 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
   const size_t sm3 = smem_bfit(g, lag_store);
   auto kb = lag_store ? kstap::k_bfit<P, Q, R, true> : kstap::k_bfit<P, Q, R, false>;
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-  const int g3 = grid_for(kb, kstap::kThreads, sm3, JL.ntiles[kstap::kKindBfit], sm_count, waves);
+  constexpr int nt3 = kstap::bfit_threads(Q);
+  const int g3 = grid_for(kb, nt3, sm3, JL.ntiles[kstap::kKindBfit], sm_count, waves);
   prof_collect(prof, KSTAP_K_BFIT);
   prof_begin(prof, KSTAP_K_BFIT, s);
-  kb<<<g3, kstap::kThreads, sm3, s>>>(g, JL, aw, Lw);
+  kb<<<g3, nt3, sm3, s>>>(g, JL, aw, Lw);
   prof_end(prof, KSTAP_K_BFIT, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;

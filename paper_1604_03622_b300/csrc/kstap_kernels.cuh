@@ -293,12 +293,28 @@ __device__ __forceinline__ longlong2 ring_sum(const longlong2* __restrict__ Vo,
   return make_longlong2(lr, li);
 }
 
-// Exact split of a 64-bit integer into a float-float pair, scaled by 2^-60.
+// Exact integer < 2^23 as a float: OR it into the mantissa of 2^23 and
+// subtract 2^23 (bit-level construction, no conversion instruction).
+__device__ __forceinline__ float small_u2f(unsigned t) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | t), 8388608.f);
+}
+
+// A 64-bit integer |v| < 2^62 as a float-float pair scaled by 2^-60, to
+// ~2^-48 relative.  v = t2 2^42 + t1 2^21 + t0 with 21-bit pieces, each
+// converted exactly; the pieces are then summed error-free (two_sum).  Only
+// 32-bit integer and single-precision operations: 64-bit integer <-> float
+// conversions would run on the (narrow) FP64 pipe.
 __device__ __forceinline__ void ll_to_ff(long long v, float& hi, float& lo) {
-  const float h = __ll2float_rn(v);
-  const long long rest = v - __float2ll_rn(h);
-  hi = h * kLagNorm;
-  lo = __ll2float_rn(rest) * kLagNorm;
+  const int t2 = (int)(v >> 42);                                   // in [-2^20, 2^20)
+  const unsigned t1 = (unsigned)((unsigned long long)v >> 21) & 0x1FFFFFu;
+  const unsigned t0 = (unsigned)v & 0x1FFFFFu;
+  const float f2 = __fmul_rn(__fsub_rn(small_u2f((unsigned)(t2 + 0x400000)), 4194304.f),
+                             3.814697265625e-06f);                 // 2^-18
+  const float f1 = __fmul_rn(small_u2f(t1), 1.8189894035458565e-12f);   // 2^-39
+  const float f0 = __fmul_rn(small_u2f(t0), kLagNorm);                  // 2^-60
+  float s, e;
+  two_sum(f2, f1, s, e);
+  quick_two_sum(s, __fadd_rn(e, f0), hi, lo);
 }
 
 constexpr int kMomRows = 4;                         // cell rows per CTA in the moments pass
@@ -521,8 +537,11 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
 // Cyclic Jacobi on an N x N Hermitian matrix held in registers (FP32).  On
 // return d[] holds the eigenvalues and the columns of U the eigenvectors,
 // sorted by decreasing eigenvalue.
-template <int N>
-__device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]) {
+// WANT_U = false skips the eigenvector accumulation (eigenvalues only);
+// sweeps stop once sum_{i<j} |A_ij|^2 <= tol * sum_i A_ii^2.
+template <int N, bool WANT_U = true>
+__device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N],
+                             float tol = 1e-14f) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -535,7 +554,7 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
 #pragma unroll
       for (int j = i + 1; j < N; ++j) off += cabs2(A[i][j]);
     }
-    if (off <= 1e-14f * diag) break;
+    if (off <= tol * diag) break;
 #pragma unroll
     for (int p = 0; p < N - 1; ++p) {
 #pragma unroll
@@ -567,11 +586,13 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
         A[q][p] = make_float2(0.f, 0.f);
         A[p][p].y = 0.f;
         A[q][q].y = 0.f;
+        if (WANT_U) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {   // U <- U G
-          const float2 up = U[k][p], uq = U[k][q];
-          U[k][p] = cadd(cmul(up, gpp), cmul(uq, gqp));
-          U[k][q] = cadd(cmul(up, gpq), cmul(uq, gqq));
+          for (int k = 0; k < N; ++k) {   // U <- U G
+            const float2 up = U[k][p], uq = U[k][q];
+            U[k][p] = cadd(cmul(up, gpp), cmul(uq, gqp));
+            U[k][q] = cadd(cmul(up, gpq), cmul(uq, gqq));
+          }
         }
       }
     }
@@ -840,6 +861,9 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   __syncwarp();
   b_times_v_fp32<Q, R>(Bc, j, Vs, y);
   __syncwarp();
+  // Gram-Schmidt keeps orthonormality to ~eps cond(B V), which the change
+  // measure of the float-float step below relies on (a one-pass Cholesky-QR
+  // of the unnormalised start would leave ~eps cond^2)
   orthonormalise_g<Q, R>(y);
 #pragma unroll
   for (int m = 0; m < R; ++m) v[m] = y[m];
@@ -943,7 +967,9 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
       for (int mp = 0; mp < R; ++mp) Hh[m][mp] = H[m][mp];
     float dd[R];
     float2 UU[R][R];
-    jacobi_small<R>(Hh, dd, UU);
+    // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
+    // by ~1e-10 lambda_1^2 / gap
+    jacobi_small<R, false>(Hh, dd, UU, 1e-10f);
 #pragma unroll
     for (int m = 0; m < R; ++m) lam[m] = dd[m];
   }
@@ -954,12 +980,66 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   }
 }
 
+// Threads of a B-pass CTA: 512 at q = 32, where the tile's B matrices fill
+// most of shared memory and one CTA per SM must bring its own 16 warps.
+__host__ __device__ constexpr int bfit_threads(int q) { return q >= 32 ? 512 : kThreads; }
+
+// 16-byte asynchronous global -> shared copy; valid == false zero-fills the
+// destination (src is then not read but must still be a mapped address).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One B entry, float-float: sum_J conj(a_J) L_J with a single precision and L
+// float-float (re_hi, re_lo, im_hi, im_lo).  With NCH = 2, even and odd J
+// accumulate in separate compensated sums (two independent dependency
+// chains, for CTAs whose threads hold one entry each), merged at the end with
+// an error-free two_sum.
+template <int NCH>
+struct BAcc {
+  float sr[2] = {0.f, 0.f}, cr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f}, ci[2] = {0.f, 0.f};
+  __device__ __forceinline__ void add(int k, float2 a, float4 L) {
+    acc_ffxf(sr[k], cr[k], L.x, L.y, a.x);     // conj(a) L: re = ar Lr + ai Li
+    acc_ffxf(sr[k], cr[k], L.z, L.w, a.y);
+    acc_ffxf(si[k], ci[k], L.z, L.w, a.x);     //            im = ar Li - ai Lr
+    acc_ffxf(si[k], ci[k], L.x, L.y, -a.y);
+  }
+  __device__ __forceinline__ float4 get() const {
+    if (NCH == 1) {
+      const ff re = ff_make(sr[0], cr[0]), im = ff_make(si[0], ci[0]);
+      return make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    float s, e;
+    two_sum(sr[0], sr[1], s, e);
+    const ff re = ff_make(s, __fadd_rn(e, __fadd_rn(cr[0], cr[1])));
+    two_sum(si[0], si[1], s, e);
+    const ff im = ff_make(s, __fadd_rn(e, __fadd_rn(ci[0], ci[1])));
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+};
+
+constexpr int kLagStages = 4;   // lag-store prefetch depth of the B pass
+
+// CTA = one row of tc cells.  B phase: for each lag, the tile's lag sums
+// (read from the lag store with a double-buffered cp.async prefetch of the
+// next lag, or recomputed from Y) are contracted with each cell's a into the
+// diagonal of B, two entries per thread at a time (independent float-float
+// chains).  Eigen phase: one group of Q lanes per cell.
 template <int P, int Q, int R, bool FROM_STORE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(bfit_threads(Q))
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
   constexpr int CPW = 32 / Q;   // cells per warp in the eigen phase
+  constexpr int NT = bfit_threads(Q);
   extern __shared__ __align__(16) unsigned char smem[];
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindBfit]; tile += gridDim.x) {
   int lt;
@@ -980,16 +1060,36 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   const size_t ncell = (size_t)JL.NC;
   float4* Bs = reinterpret_cast<float4*>(smem);                 // [TC][NB]
   float2* as = reinterpret_cast<float2*>(Bs + TC * NB);         // [TC][PP]
-  float4* lag = reinterpret_cast<float4*>(as + TC * PP);        // [PP][NUmax]
+  float4* lag = reinterpret_cast<float4*>(as + TC * PP);        // [kLagStages or 1][PP][NUmax]
   float2* Vs = reinterpret_cast<float2*>(lag);                  // eigen phase: [warps * CPW][Q][R]
-  longlong2* Vo = reinterpret_cast<longlong2*>(lag + PP * NUmax);
+  longlong2* Vo = reinterpret_cast<longlong2*>(lag + PP * NUmax);   // recompute only
   longlong2* Vg = Vo + PP * WT;
   int2* Yq = reinterpret_cast<int2*>(Vg + PP * WT);
 
   const int sh = frame_shift(*maxbits, g.B);
   const float scale = ldexpf(1.f, sh);
-  if (!FROM_STORE) load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
-  for (int idx = threadIdx.x; idx < TC * PP; idx += blockDim.x) {
+  const int WL = g.W + Q - 1;
+  // prefetch of lag lg into buffer buf: rows J of the store are contiguous
+  // in u, positions past the row end are zero-filled
+  auto prefetch = [&](int lg, int buf) {
+    const int NU = TC + Q - 1 - lg;
+    const float4* src = Lw + ((size_t)r * Q + lg) * PP * WL;
+    float4* dst = lag + buf * PP * NUmax;
+    for (int idx = threadIdx.x; idx < PP * NU; idx += NT) {
+      const int u = idx % NU, J = idx / NU;
+      const bool ok = c0 + u < WL;
+      cp_async16(dst + J * NUmax + u, ok ? src + (size_t)J * WL + c0 + u : src, ok);
+    }
+    cp_async_commit();
+  };
+  if (FROM_STORE) {
+#pragma unroll
+    for (int st = 0; st < kLagStages; ++st)
+      if (st < Q) prefetch(st, st);
+  } else {
+    load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
+  }
+  for (int idx = threadIdx.x; idx < TC * PP; idx += NT) {
     const int cl = idx / PP, J = idx % PP;
     const int c = c0 + cl;
     as[idx] = (c < g.W) ? aw[J * ncell + (size_t)JB.cell0 + (size_t)r * g.W + c]
@@ -997,21 +1097,26 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   }
   __syncthreads();
 
-  const int WL = g.W + Q - 1;
   for (int lagg = 0; lagg < Q; ++lagg) {
     const int NU = TC + Q - 1 - lagg;
+    const float4* lb = lag;
     if (FROM_STORE) {
-      const float4* src = Lw + ((size_t)r * Q + lagg) * PP * WL;
-      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
-        const int u = idx % NU, J = idx / NU;
-        lag[J * NUmax + u] =
-            (c0 + u < WL) ? __ldg(src + (size_t)J * WL + c0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      // groups committed so far: lags 0 .. min(lagg + kLagStages - 1, Q - 1)
+      const int ahead = min(kLagStages - 1, Q - 1 - lagg);
+      if (ahead >= 3)
+        cp_async_wait<3>();
+      else if (ahead == 2)
+        cp_async_wait<2>();
+      else if (ahead == 1)
+        cp_async_wait<1>();
+      else
+        cp_async_wait<0>();
+      lb = lag + (lagg % kLagStages) * PP * NUmax;
     } else {
       const int KW = NU + 2 * g.Ra;
       vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
+      for (int idx = threadIdx.x; idx < PP * NU; idx += NT) {
         const int u = idx % NU, J = idx / NU;
         const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
         float4 v;
@@ -1021,31 +1126,26 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
       }
     }
     __syncthreads();
-    // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float
-    const int nj = Q - lagg;
-    for (int idx = threadIdx.x; idx < TC * nj; idx += blockDim.x) {
+    // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float.  Positions
+    // the prefetch zero-filled are read only by cells past the frame edge.
+    const int nj = Q - lagg, tot = TC * nj;
+    for (int idx = threadIdx.x; idx < tot; idx += NT) {
       const int cl = idx / nj, j = idx % nj;
-      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+      constexpr int NCH = (Q >= 32) ? 2 : 1;   // q = 32: tot <= NT, one entry per thread
+      BAcc<NCH> b;
 #pragma unroll
-      for (int J = 0; J < PP; ++J) {
-        const float2 a = as[cl * PP + J];
-        const float4 L = lag[J * NUmax + cl + j];
-        acc_ffxf(sr, cr, L.x, L.y, a.x);     // conj(a) L: re = ar Lr + ai Li
-        acc_ffxf(sr, cr, L.z, L.w, a.y);
-        acc_ffxf(si, ci, L.z, L.w, a.x);     //            im = ar Li - ai Lr
-        acc_ffxf(si, ci, L.x, L.y, -a.y);
-      }
-      const ff re = ff_make(sr, cr), im = ff_make(si, ci);
-      Bs[cl * NB + diag_off<Q>(lagg) + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      for (int J = 0; J < PP; ++J) b.add(NCH == 2 ? (J & 1) : 0, as[cl * PP + J], lb[J * NUmax + cl + j]);
+      Bs[cl * NB + diag_off<Q>(lagg) + j] = b.get();
     }
     __syncthreads();
+    if (FROM_STORE && lagg + kLagStages < Q) prefetch(lagg + kLagStages, lagg % kLagStages);
   }
 
   // eigen phase: a group of Q lanes per cell
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / Q, j = lane % Q;
   const int slot = warp * CPW + sub;
-  const int per_pass = (kThreads / 32) * CPW;
+  const int per_pass = (NT / 32) * CPW;
   for (int base = 0; base < TC; base += per_pass) {
     const int cl = base + slot;
     const bool live = cl < TC && (c0 + cl) < g.W;
