@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kstap", choices=["kstap", "reference"])
     ap.add_argument("--workload", default="frame1024")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "bf16x3"],
+                    help="arithmetic of the velocity-bank contraction (fp32: CUDA cores; "
+                         "fp16x3 / bf16x3: tensor cores, hi + lo splits)")
     ap.add_argument("--cpu-sample", type=int, default=1024,
                     help="cells of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -362,6 +365,7 @@ def main():
     Ys = [torch.from_numpy(f.Y).to(dev) for f in frames]
     stream = torch.cuda.current_stream(dev)
     ks = KStap.from_workload(wl, frames[0].bank_a, frames[0].bank_b, device=str(dev),
+                             precision=args.precision,
                              stream=stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ncell = wl.H * wl.W
@@ -470,8 +474,10 @@ def main():
     line = dict(
         metric=METRIC, value=value, unit="cells/s", n_gpus=ws, steps=args.steps,
         warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype="f32+ff/i64", data="synthetic",
-        config=dict(workload=wl.name, path="plain", cells_per_frame=ncell, p=wl.p, q=wl.q,
+        scaling="weak", vs_baseline=None, dtype="f32+ff/i64" + ("" if args.precision == "fp32" else "+" + args.precision),
+        data="synthetic",
+        config=dict(workload=wl.name, path="plain", precision=args.precision, cells_per_frame=ncell,
+                    p=wl.p, q=wl.q,
                     r_a=wl.r_a, r_b=wl.r_b, n=wl.n, V=wl.V, cnr_db=wl.cnr_db,
                     l2="256 MiB flush between timed steps, outside the events",
                     parallelism=f"replicas x{ws}"),

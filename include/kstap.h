@@ -76,7 +76,16 @@ typedef struct {
   double eps;
   int max_iter;
   float tau;
+  /* Arithmetic of the velocity-bank contraction (Eq. KronSTAP statistic):
+   * KSTAP_FP32 (CUDA cores; T within 1e-4 of FP64), or the tensor-core route
+   * KSTAP_FP16X3 / KSTAP_BF16X3 (tcgen05 MMA on hi + lo 16-bit splits of
+   * the projected snapshot and the bank, FP32 accumulation; near-blind
+   * velocities fall back to the CUDA-core arithmetic).  The tensor-core
+   * route needs V <= 128.  The fit (steps 1-2) is the same for all three. */
+  int precision;
 } kstap_params;
+
+enum { KSTAP_FP32 = 0, KSTAP_FP16X3 = 1, KSTAP_BF16X3 = 2 };
 
 /* Per-cell LR-Kron factors, caller-owned device arrays of H * W cells each.
  *   UA    : [k][p][r_a]  complex64, orthonormal columns (U_A of Eq. KronSTAP)
@@ -140,6 +149,12 @@ kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long
 kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in,
                           const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
                           float* T_all);
+
+/* Waits for the context stream, then reports whether any kernel on this
+ * device gave up a bounded wait for its tensor-core work (KSTAP_ECUDA, with
+ * the reason in kstap_last_error; the word is cleared) or not (KSTAP_OK).
+ * Results of a launch that gave up are not valid. */
+kstap_status kstap_device_status(kstap_ctx* ctx);
 
 /* Free the context, its workspace and its copies of the bank. */
 kstap_status kstap_destroy(kstap_ctx* ctx);

@@ -24,7 +24,7 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
-            "kstap_release", "kstap_fit_report"]
+            "kstap_release", "kstap_fit_report", "kstap_device_status"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -32,7 +32,7 @@ class KstapParams(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("r_a", ctypes.c_int),
                 ("r_b", ctypes.c_int), ("ring_r", ctypes.c_int), ("ring_a", ctypes.c_int),
                 ("guard_r", ctypes.c_int), ("guard_a", ctypes.c_int), ("eps", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("tau", ctypes.c_float)]
+                ("max_iter", ctypes.c_int), ("tau", ctypes.c_float), ("precision", ctypes.c_int)]
 
 
 class KstapFactors(ctypes.Structure):
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.kstap_submit.argtypes = [P, P, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
         L.kstap_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KstapResult), I]
         L.kstap_release.argtypes = [P, ctypes.c_uint64]
+        L.kstap_device_status.argtypes = [P]
         L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]
         L.kstap_set_profiling.argtypes = [P, I]
@@ -111,7 +112,7 @@ def lib() -> ctypes.CDLL:
                      "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
                      "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
-                     "kstap_fit_report"):
+                     "kstap_fit_report", "kstap_device_status"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -127,10 +128,13 @@ def _ptr(t) -> Optional[int]:
     return None if t is None else int(t.data_ptr())
 
 
+PRECISION = {"fp32": 0, "fp16x3": 1, "bf16x3": 2}
+
+
 def make_params(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, tau, eps=0.0,
-                max_iter=0) -> KstapParams:
+                max_iter=0, precision="fp32") -> KstapParams:
     return KstapParams(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, float(eps),
-                       int(max_iter), float(tau))
+                       int(max_iter), float(tau), PRECISION[precision])
 
 
 def kstap_create(params: KstapParams, bank_a, bank_b, V: int, hbm_budget_bytes: int = 0,
@@ -159,6 +163,11 @@ def kstap_fit_report(ctx: int):
     if st != KSTAP_WARN_NOCONV:
         _check(st, ctx)
     return int(nc.value), int(nf.value)
+
+
+def kstap_device_status(ctx: int) -> None:
+    """Raises if a kernel gave up a bounded wait for its tensor-core work."""
+    _check(lib().kstap_device_status(ctx), ctx)
 
 
 def kstap_detect(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors, Tmax, vidx, map_,

@@ -22,6 +22,7 @@
 
 #include "../../include/kstap.h"
 #include "kstap_kernels.cuh"
+#include "kstap_tc.cuh"
 
 using kstap::Geom;
 using kstap::Job;
@@ -46,6 +47,10 @@ struct kstap_ctx {
   float2* bank_aT = nullptr;
   float2* bank_bT = nullptr;
   float* bank_n2 = nullptr;
+  // tensor-core route: bank operand image (hi, lo; tcgen05 K-major layout)
+  // and the inverse of its power-of-two scale
+  uint4* bank_op = nullptr;
+  float bank_inv = 1.f;
   // workspace and the device job table of kstap_run_batch
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -171,6 +176,11 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "(2 ring_r + 1)(2 ring_a + 1) must be <= 1024";
     return false;
   }
+  if (p->precision != KSTAP_FP32 && p->precision != KSTAP_FP16X3 &&
+      p->precision != KSTAP_BF16X3) {
+    why = "precision must be KSTAP_FP32, KSTAP_FP16X3 or KSTAP_BF16X3";
+    return false;
+  }
   return true;
 }
 
@@ -239,8 +249,8 @@ int tiles_moments(int H, int W) {
 int tiles_flip(int H, int W) { return (int)(((size_t)H * W + 127) / 128); }
 int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
 int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
-int tiles_detect(int H, int W, int q) {
-  const int c = cells_per_detect_block(q);
+int tiles_detect(int H, int W, int q, int precision = KSTAP_FP32) {
+  const int c = precision == KSTAP_FP32 ? cells_per_detect_block(q) : kstap::kTcCells;
   return (int)(((size_t)H * W + c - 1) / c);
 }
 
@@ -326,7 +336,7 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
     t[0] += tiles_moments(j.H, j.W);
     t[1] += tiles_flip(j.H, j.W);
     t[2] += tiles_bfit(j.H, j.W, g.tc);
-    t[3] += tiles_detect(j.H, j.W, p.q);
+    t[3] += tiles_detect(j.H, j.W, p.q, p.precision);
     jobs.push_back(j);
   }
   memset(&JL, 0, sizeof(JL));
@@ -441,10 +451,31 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
   return KSTAP_OK;
 }
 
+template <int P, int Q, int R, bool BF16>
+kstap_status enqueue_detect_tc(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                               int sm_count, int waves, cudaStream_t s) {
+  auto k = kstap::k_detect_tc<P, Q, R, BF16>;
+  const size_t sm = kstap::tc_smem_request(P, Q, R);
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  constexpr int nt = kstap::tc_threads(Q);
+  const int grid = grid_for(k, nt, sm, JL.ntiles[kstap::kKindDetect], sm_count, waves);
+  prof_collect(prof, KSTAP_K_DETECT);
+  prof_begin(prof, KSTAP_K_DETECT, s);
+  k<<<grid, nt, sm, s>>>(g, JL, ctx->bank_op, ctx->bank_inv, ctx->bank_aT, ctx->bank_bT,
+                         ctx->bank_n2);
+  prof_end(prof, KSTAP_K_DETECT, s);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+  return KSTAP_OK;
+}
+
 template <int P, int Q, int R>
 kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                             int sm_count, int waves, cudaStream_t s) {
   if (JL.njobs < 1) return KSTAP_OK;
+  if (ctx->prm.precision == KSTAP_FP16X3)
+    return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
+  if (ctx->prm.precision == KSTAP_BF16X3)
+    return enqueue_detect_tc<P, Q, R, true>(ctx, prof, g, JL, sm_count, waves, s);
   const size_t sm = smem_detect(g);
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -636,6 +667,48 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
   if (e != cudaSuccess) {
     kstap_destroy(ctx);
     return fail(nullptr, KSTAP_ECUDA, "bank upload failed: %s", cudaGetErrorString(e));
+  }
+  if (params->precision != KSTAP_FP32) {
+    if (V > kstap::kTcM) {
+      kstap_destroy(ctx);
+      return fail(nullptr, KSTAP_EINVAL, "the tensor-core route needs V <= %d", kstap::kTcM);
+    }
+    // Bank operand of the tensor-core GEMM: row v = (Re b_v, Im b_v) scaled by a
+    // power of two s (max |component| s in [0.5, 1)), split hi + lo into
+    // 16-bit floats and laid out as the kernel's shared-memory image.
+    float bmax = 0.f;
+    for (const kstap_c64& z : hb) bmax = std::max(bmax, std::max(std::fabs(z.re), std::fabs(z.im)));
+    const float sc = (bmax > 0.f && std::isfinite(bmax)) ? std::ldexp(1.f, -(std::ilogb(bmax) + 1)) : 1.f;
+    ctx->bank_inv = 1.f / sc;
+    const int K2 = 2 * q;
+    const size_t half = (size_t)kstap::kTcM * K2 * 2;   // bytes of one 16-bit image
+    std::vector<uint16_t> img(2 * half / 2, 0);
+    const bool bf = params->precision == KSTAP_BF16X3;
+    for (int v = 0; v < V; ++v)
+      for (int k = 0; k < K2; ++k) {
+        const kstap_c64 z = hb[(size_t)v * q + (k % q)];
+        const float x = (k < q ? z.re : z.im) * sc;
+        uint16_t h, l;
+        if (bf) {
+          const __nv_bfloat16 hh = __float2bfloat16_rn(x);
+          h = __bfloat16_as_ushort(hh);
+          l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
+        } else {
+          const __half hh = __float2half_rn(x);
+          h = __half_as_ushort(hh);
+          l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+        }
+        const size_t off = kstap::tc_off(v, k, kstap::kTcM) / 2;
+        img[off] = h;
+        img[half / 2 + off] = l;
+      }
+    e = cudaMalloc(&ctx->bank_op, 2 * half);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ctx->bank_op, img.data(), 2 * half, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      kstap_destroy(ctx);
+      return fail(nullptr, KSTAP_ECUDA, "bank operand upload failed: %s", cudaGetErrorString(e));
+    }
   }
   *out = ctx;
   return KSTAP_OK;
@@ -959,7 +1032,20 @@ kstap_status kstap_destroy(kstap_ctx* ctx) {
   cudaFree(ctx->bank_bT);
   cudaFree(ctx->bank_n2);
   cudaFree(ctx->report);
+  cudaFree(ctx->bank_op);
   delete ctx;
+  return KSTAP_OK;
+}
+
+kstap_status kstap_device_status(kstap_ctx* ctx) {
+  if (!ctx) return KSTAP_EINVAL;
+  KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  unsigned f = 0, z = 0;
+  KSTAP_CUDA(ctx, cudaMemcpyFromSymbol(&f, kstap::g_fault, sizeof(f)));
+  if (f) {
+    KSTAP_CUDA(ctx, cudaMemcpyToSymbol(kstap::g_fault, &z, sizeof(z)));
+    return fail(ctx, KSTAP_ECUDA, "a tensor-core completion wait gave up (fault word 0x%x)", f);
+  }
   return KSTAP_OK;
 }
 
