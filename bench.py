@@ -67,6 +67,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(seed: int, rank: int, s: int) -> int:
+    """Seed of frame s of a rank: every rank works on its own frames."""
+    return seed + 7919 * rank + s
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Max of a per-rank time over all ranks (the job is as slow as its
+    slowest rank); a barrier-like host collective, not on the data path."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_frame: int, steps: int, ws: int, total_ms: float) -> float:
+    """Whole-job throughput under weak scaling: each of the ws ranks processed
+    `steps` frames of `cells_per_frame` cells in at most total_ms."""
+    return cells_per_frame * steps * ws / (total_ms / 1e3)
+
+
 # ----------------------------------------------------------- reference arm --
 def run_reference(args):
     import gen
@@ -184,11 +207,13 @@ def work_per_cell(wl):
 
 
 # ------------------------------------------------------- batched vs plain ---
-def batched_leg(dev, steps: int, warmup: int):
+def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
     """256 uneven tiles (q in {8,16,32}, r_b in {2,3,4}): plain = one tile at a
     time through kstap_fit_project + kstap_detect (5 launches per tile, no
-    overlap); batched = one CUDA graph holding one autotuned batch per (q, r_b)
-    class on parallel branches.  Both compute the same bits (tested)."""
+    overlap, FP32 bank); batched = one CUDA graph holding one autotuned batch
+    per (q, r_b) class on parallel branches, bank on the tensor cores
+    (`precision`).  The fits are bit-identical; T agrees to the 16-bit route's
+    bar (tested)."""
     import torch
     import gen
     import paper_1604_03622_b300 as K
@@ -199,12 +224,13 @@ def batched_leg(dev, steps: int, warmup: int):
     for i, w in enumerate(tiles):
         classes.setdefault((w.q, w.r_b), []).append(i)
     keys = sorted(classes)
-    ctxs, descs, bufs, Ys = {}, {}, {}, [None] * len(tiles)
+    ctxs, bctxs, descs, bufs, Ys = {}, {}, {}, {}, [None] * len(tiles)
     for key in keys:
         idx = classes[key]
-        ks = KStap.from_workload(tiles[idx[0]], frames[idx[0]].bank_a, frames[idx[0]].bank_b,
-                                 device=str(dev))
-        ctxs[key] = ks
+        w0, f0 = tiles[idx[0]], frames[idx[0]]
+        ctxs[key] = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev))
+        ks = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev), precision=precision)
+        bctxs[key] = ks
         for i in idx:
             Ys[i] = torch.from_numpy(frames[i].Y).to(dev)
         # the descriptors hold raw device pointers: keep the tensors alive
@@ -213,9 +239,9 @@ def batched_leg(dev, steps: int, warmup: int):
     stream = torch.cuda.current_stream(dev)
     tuning = {}
     for key in keys:
-        t = K.kstap_autotune(ctxs[key].ctx, descs[key], reps=2)
+        t = K.kstap_autotune(bctxs[key].ctx, descs[key], reps=2)
         tuning[f"q{key[0]}_r{key[1]}"] = dict(waves=t.waves, tc=t.tc, ms=round(t.ms_per_batch, 3))
-    graph = K.kstap_graph_create([ctxs[k].ctx for k in keys], [descs[k] for k in keys])
+    graph = K.kstap_graph_create([bctxs[k].ctx for k in keys], [descs[k] for k in keys])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ncells = sum(w.cells for w in tiles)
 
@@ -241,25 +267,27 @@ def batched_leg(dev, steps: int, warmup: int):
     plain_ms = timed(plain)
     batched_ms = timed(lambda: K.kstap_graph_launch(graph, stream.cuda_stream))
     K.kstap_graph_destroy(graph)
-    for ks in ctxs.values():
+    for ks in list(ctxs.values()) + list(bctxs.values()):
         ks.close()
     pm, bm = sum(plain_ms) / len(plain_ms), sum(batched_ms) / len(batched_ms)
     return dict(workload="tiles256", tiles=len(tiles), cells=ncells, classes=len(keys),
                 plain=dict(cells_per_s=ncells / (pm / 1e3), ms_per_batch=pm,
-                           p99_ms=sorted(plain_ms)[-1], kernel_launches=5 * len(tiles)),
+                           p99_ms=sorted(plain_ms)[-1], kernel_launches=5 * len(tiles),
+                           precision="fp32"),
                 batched=dict(cells_per_s=ncells / (bm / 1e3), ms_per_batch=bm,
                              p99_ms=sorted(batched_ms)[-1], graph_launches=1,
-                             kernel_launches=5 * len(keys)),
+                             kernel_launches=5 * len(keys), precision=precision),
                 speedup=pm / bm, tuning=tuning)
 
 
 # ----------------------------------------------------------------- serving ---
-def serving_leg(dev, n_requests: int):
+def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
     """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
     V = 64) at 0.8 x the measured plain capacity, through kstap_submit /
     kstap_poll with a 120 GB HBM budget (60 GB per q class).  plain: one frame
-    at a time (batch 1, one stream); batched: continuous batching (batch <= 16,
-    4 streams).  Latency = completion - arrival."""
+    at a time (batch 1, one stream, FP32 bank); batched: continuous batching
+    (batch <= 16, 4 streams, bank on the tensor cores).  Latency = completion
+    - arrival."""
     import threading
     import torch
     import gen
@@ -289,12 +317,13 @@ def serving_leg(dev, n_requests: int):
     rate = 0.8 / float(np.mean(per_frame_s))
     t_arr, pick = gen.poisson_arrivals(n_requests, rate, len(pool))
 
-    def run(max_batch, max_inflight):
+    def run(max_batch, max_inflight, prec):
         ctxs = {}
         for q in qs:
             i0 = [i for i, w in enumerate(pool) if w.q == q][0]
             ks = KStap.from_workload(pool[i0], frames[i0].bank_a, frames[i0].bank_b,
-                                     device=str(dev), hbm_budget_bytes=budget // len(qs))
+                                     device=str(dev), hbm_budget_bytes=budget // len(qs),
+                                     precision=prec)
             K.kstap_serve_config(ks.ctx, max_batch, max_inflight)
             ctxs[q] = ks
         tickets = [None] * n_requests
@@ -330,10 +359,10 @@ def serving_leg(dev, n_requests: int):
         return dict(cells_per_s=cells / t_end, p50_ms=lat[len(lat) // 2],
                     p99_ms=lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                     mean_ms=float(np.mean(lat)), wall_s=t_end, max_batch=max_batch,
-                    streams=max_inflight)
+                    streams=max_inflight, precision=prec)
 
-    plain = run(1, 1)
-    batched = run(16, 4)
+    plain = run(1, 1, "fp32")
+    batched = run(16, 4, precision)
     return dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
                 q=qs, r_b=3, V=64, budget_gb=120, arrival_rate_hz=rate,
                 plain_capacity_frames_per_s=1.0 / float(np.mean(per_frame_s)),
@@ -361,7 +390,7 @@ def main():
     wl = gen.WORKLOADS[args.workload]
     if args.cells:
         wl = wl.with_size(*args.cells)
-    frames = [gen.make_frame(wl, seed=wl.seed + 7919 * rank + s) for s in range(2)]
+    frames = [gen.make_frame(wl, seed=rank_seed(wl.seed, rank, s)) for s in range(2)]
     Ys = [torch.from_numpy(f.Y).to(dev) for f in frames]
     stream = torch.cuda.current_stream(dev)
     ks = KStap.from_workload(wl, frames[0].bank_a, frames[0].bank_b, device=str(dev),
@@ -396,12 +425,8 @@ def main():
     kt = K.kstap_kernel_times(ks.ctx)
     K.kstap_set_profiling(ks.ctx, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ncell * args.steps * ws / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    value = job_value(ncell, args.steps, ws, total_ms)
 
     # ---- e2e: pinned host frame in, Tmax / vidx / map out, through the C ABI
     Yh = [torch.from_numpy(f.Y).pin_memory() for f in frames]
@@ -422,12 +447,8 @@ def main():
         b.synchronize()
         if s >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms) if e2e_ms else float("nan")
-    if ws > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ncell * args.steps * ws / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), ws, dev)
+    e2e_value = job_value(ncell, args.steps, ws, e2e_total)
     h2d = frames[0].Y.nbytes
     d2h = ncell * (4 + 4 + 1)
 

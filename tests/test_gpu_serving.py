@@ -37,7 +37,8 @@ class _DevArray:
                                              version=3)
 
 
-def test_served_results_equal_alone_and_in_the_mix():
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_served_results_equal_alone_and_in_the_mix(precision):
     import torch
     import paper_1604_03622_b300 as K
     from paper_1604_03622_b300.runner import KStap
@@ -45,7 +46,8 @@ def test_served_results_equal_alone_and_in_the_mix():
     sizes = [(40, 70), (13, 29), (64, 33), (7, 7), (50, 90), (21, 61)]
     frames = [gen.make_frame(base.with_size(H, W), seed=base.seed + 500 + k)
               for k, (H, W) in enumerate(sizes)]
-    ks = KStap.from_workload(frames[0].wl, frames[0].bank_a, frames[0].bank_b)
+    ks = KStap.from_workload(frames[0].wl, frames[0].bank_a, frames[0].bank_b,
+                             precision=precision)
     Ys = [torch.from_numpy(f.Y).cuda() for f in frames]
     alone = []
     for Y in Ys:

@@ -75,3 +75,48 @@ def test_tc_rejects_large_bank():
     a, b = gen.steering_bank(wl.p, wl.q, 160)
     with pytest.raises(K.KstapError, match="EINVAL"):
         KStap.from_workload(wl, a, b, precision="fp16x3")
+
+
+def test_tc_batch_and_graph_bit_identical_to_per_frame():
+    """Batches and CUDA graphs of the tensor-core route reproduce the per-frame
+    calls bit for bit, whatever the launch tuning (no atomics in value paths;
+    the near-blind queue order does not change any value)."""
+    import torch
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    keys = ("Tmax", "vidx", "map", "T_all", "UB_hi")
+    groups = []
+    for name, sizes, seed0 in (("frame1024", [(7, 40), (33, 29), (1, 1), (20, 70)], 0),
+                               ("precision2048", [(6, 40), (11, 17)], 7)):
+        base = gen.WORKLOADS[name]
+        fr = [gen.make_frame(base.with_size(H, W), seed=base.seed + 300 + seed0 + k)
+              for k, (H, W) in enumerate(sizes)]
+        ks = KStap.from_workload(fr[0].wl, fr[0].bank_a, fr[0].bank_b, precision="fp16x3")
+        Ys = [torch.from_numpy(f.Y).cuda() for f in fr]
+        ref = [{k: v.cpu().numpy() for k, v in ks.run(Y, T_all=True).items() if k in keys}
+               for Y in Ys]
+        groups.append((ks, Ys, ref))
+    for ks, Ys, ref in groups:
+        for waves, tc in ((1, 16), (16, 0)):
+            K.kstap_set_tuning(ks.ctx, waves, tc)
+            bufs = [ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
+            K.kstap_run_batch(ks.ctx, [ks.frame_desc(Y, b) for Y, b in zip(Ys, bufs)])
+            torch.cuda.synchronize()
+            for r, b in zip(ref, bufs):
+                for k in keys:
+                    assert np.array_equal(b[k].cpu().numpy(), r[k]), (waves, tc, k)
+    bufs = [[ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
+            for ks, Ys, _ in groups]
+    descs = [[ks.frame_desc(Y, b) for Y, b in zip(Ys, bg)]
+             for (ks, Ys, _), bg in zip(groups, bufs)]
+    graph = K.kstap_graph_create([g[0].ctx for g in groups], descs)
+    K.kstap_graph_launch(graph, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for (ks, Ys, ref), bg in zip(groups, bufs):
+        for r, b in zip(ref, bg):
+            for k in keys:
+                assert np.array_equal(b[k].cpu().numpy(), r[k]), k
+    K.kstap_graph_destroy(graph)
+    for ks, _, _ in groups:
+        K.kstap_device_status(ks.ctx)
+        ks.close()
