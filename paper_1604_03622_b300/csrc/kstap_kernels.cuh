@@ -727,21 +727,40 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
     bad = box_nonfinite(JB.Y, gj, (int)(local / JB.W), (int)(local % JB.W), 0, 1);
     if (JL.report) count_lanes(JL.report + 1, bad);
   }
-  // eta^2 = 1 - a^H M a / (|a|^2 tr M) for b matched to the final a
-  double tr = 0.0, aMa = 0.0, an = 0.0;
+  // eta^2 = 1 - a^H M a / (|a|^2 tr M) for b matched to the final a, with the
+  // three sums in float-float (the ratio is 1 - eta^2, so eta << 1 cancels):
+  // a^H M a = sum_J M_JJ |a_J|^2 + 2 Re sum_{J<J'} conj(a_J) M_JJ' a_J'
+  float trs = 0.f, trc = 0.f, ans = 0.f, anc = 0.f, qs = 0.f, qc = 0.f;
 #pragma unroll
   for (int J = 0; J < PP; ++J) {
-    tr += (double)M[tri_idx(PP, J, J)].x;
-    an += (double)cabs2(a[J]);
-    double sr = 0.0, si = 0.0;
+    const float d = M[tri_idx(PP, J, J)].x;
+    float t, e;
+    two_sum(trs, d, t, e);
+    trs = t;
+    trc = __fadd_rn(trc, e);
+    float p, pe;
+    two_prod(a[J].x, a[J].x, p, pe);            // |a_J|^2 exactly, as two pairs
+    acc_ffxf(ans, anc, p, pe, 1.f);
+    acc_ffxf(qs, qc, p, pe, d);
+    two_prod(a[J].y, a[J].y, p, pe);
+    acc_ffxf(ans, anc, p, pe, 1.f);
+    acc_ffxf(qs, qc, p, pe, d);
 #pragma unroll
-    for (int Jp = 0; Jp < PP; ++Jp) {
-      const float2 m = (J <= Jp) ? M[tri_idx(PP, J, Jp)] : cconj(M[tri_idx(PP, Jp, J)]);
-      sr += (double)m.x * a[Jp].x - (double)m.y * a[Jp].y;
-      si += (double)m.x * a[Jp].y + (double)m.y * a[Jp].x;
+    for (int Jp = J + 1; Jp < PP; ++Jp) {
+      // 2 Re(conj(a_J) m a_J') with m = M_JJ': m a_J' in float-float first
+      const float2 m = M[tri_idx(PP, J, Jp)];
+      float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+      acc_prod(rs, rc, m.x, a[Jp].x);
+      acc_prod(rs, rc, -m.y, a[Jp].y);
+      acc_prod(is, ic, m.x, a[Jp].y);
+      acc_prod(is, ic, m.y, a[Jp].x);
+      acc_ffxf(qs, qc, rs, rc, 2.f * a[J].x);
+      acc_ffxf(qs, qc, is, ic, 2.f * a[J].y);
     }
-    aMa += (double)a[J].x * sr + (double)a[J].y * si;
   }
+  const double tr = (double)trs + (double)trc;
+  const double an = (double)ans + (double)anc;
+  const double aMa = (double)qs + (double)qc;
 #pragma unroll
   for (int J = 0; J < PP; ++J) aw[J * ncell + cell] = a[J];
   float trA = 0.f;
@@ -781,8 +800,9 @@ __device__ __forceinline__ float4 b_at(const float4* __restrict__ Bc, int j, int
   return make_float4(v.x, v.y, -v.z, -v.w);
 }
 
-// Row j of B times the q x R matrix Vs ([l][R]), visiting l = (j + t) mod Q so
-// that the Q lanes of a group read consecutive shared-memory words.
+// Row j of B times the q x R matrix Vs (column-major, [m][l]: lanes read
+// consecutive words), visiting l = (j + t) mod Q so that the Q lanes of a
+// group also read consecutive entries of B.
 template <int Q, int R>
 __device__ __forceinline__ void b_times_v_fp32(const float4* __restrict__ Bc, int j,
                                                const float2* __restrict__ Vs, float2 (&y)[R]) {
@@ -794,7 +814,7 @@ __device__ __forceinline__ void b_times_v_fp32(const float4* __restrict__ Bc, in
     const float4 b = b_at<Q>(Bc, j, l);
     const float2 bh = make_float2(b.x, b.z);
 #pragma unroll
-    for (int m = 0; m < R; ++m) y[m] = cadd(y[m], cmul(bh, Vs[l * R + m]));
+    for (int m = 0; m < R; ++m) y[m] = cadd(y[m], cmul(bh, Vs[m * Q + l]));
   }
 }
 
@@ -857,7 +877,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   }
   orthonormalise_g<Q, R>(v);
 #pragma unroll
-  for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+  for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
   __syncwarp();
   b_times_v_fp32<Q, R>(Bc, j, Vs, y);
   __syncwarp();
@@ -872,7 +892,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   float2 H[R][R];
   for (int step = 0; step < 4; ++step) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) Vs[j * R + m] = v[m];
+    for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
     __syncwarp();
     float s[R][4];
 #pragma unroll
@@ -883,7 +903,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
       const float4 b = b_at<Q>(Bc, j, l);
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const float2 x = Vs[l * R + m];
+        const float2 x = Vs[m * Q + l];
         acc_ffxf(s[m][0], s[m][1], b.x, b.y, x.x);     // re = br xr - bi xi
         acc_ffxf(s[m][0], s[m][1], b.z, b.w, -x.y);
         acc_ffxf(s[m][2], s[m][3], b.x, b.y, x.y);     // im = br xi + bi xr
@@ -1297,8 +1317,10 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float best = -1.f;
   int bestv = 0x7fffffff;
   if (live) {
-    for (int v0 = gl * VB; v0 < V; v0 += G * VB) {
-      const int nv = min(VB, V - v0);
+    // lane gl takes velocities base + k G + gl: the lanes of a group read
+    // consecutive bank words, and each lane still visits its v in increasing
+    // order (lowest v wins ties)
+    for (int base = 0; base < V; base += G * VB) {
       float2 Gm[VB][R];
 #pragma unroll
       for (int k = 0; k < VB; ++k)
@@ -1312,8 +1334,8 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
         for (int m = 0; m < R; ++m) u[m] = Uh[j * R + m];
 #pragma unroll
         for (int k = 0; k < VB; ++k) {
-          if (k < nv) {
-            const float2 b = bT[j * V + v0 + k];
+          if (base + k * G + gl < V) {
+            const float2 b = bT[j * V + base + k * G + gl];
 #pragma unroll
             for (int m = 0; m < R; ++m) Gm[k][m] = cadd(Gm[k][m], cmulc(u[m], b));
           }
@@ -1337,8 +1359,8 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
         for (int i = 0; i < P; ++i) zz[i] = Zs[i * Q + j];
 #pragma unroll
         for (int k = 0; k < VB; ++k) {
-          if (k < nv) {
-            float2 w = bT[j * V + v0 + k];
+          if (base + k * G + gl < V) {
+            float2 w = bT[j * V + base + k * G + gl];
 #pragma unroll
             for (int m = 0; m < R; ++m) w = csub(w, cmul(u[m], Gm[k][m]));
             dB[k] += cabs2(w);
@@ -1352,12 +1374,12 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       // of G itself lie in span(U_B), which Z annihilates, so G stays FP32.
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
-        if (k < nv && dB[k] < kBlindRefine * nb[v0 + k]) {
+        if (base + k * G + gl < V && dB[k] < kBlindRefine * nb[base + k * G + gl]) {
           float dBn = 0.f;
 #pragma unroll
           for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
           for (int j = 0; j < Q; ++j) {
-            const float2 b = bT[j * V + v0 + k];
+            const float2 b = bT[j * V + base + k * G + gl];
             float sr = b.x, cr = 0.f, si = b.y, ci = 0.f;
 #pragma unroll
             for (int m = 0; m < R; ++m) {
@@ -1381,8 +1403,8 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       }
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
-        if (k >= nv) break;
-        const int v = v0 + k;
+        if (base + k * G + gl >= V) break;
+        const int v = base + k * G + gl;
         float2 t = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], aT[i * V + v]));
