@@ -567,31 +567,34 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
         const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
         const float c = rsqrtf(1.f + tt * tt);
         const float s = tt * c;
-        // G = diag(1, conj(ph)) [[c, s], [-s, c]]
-        const float2 gpp = make_float2(c, 0.f), gpq = make_float2(s, 0.f);
-        const float2 gqp = cscale(cconj(ph), -s), gqq = cscale(cconj(ph), c);
+        // G = diag(1, conj(ph)) [[c, s], [-s, c]]; A <- G^H A G touches only
+        // rows / columns p and q: the 2 x 2 block closes analytically
+        // (A_pp -= t |A_pq|, A_qq += t |A_pq|, A_pq = 0), the other entries
+        // of columns p, q rotate and are mirrored to keep A Hermitian
+        const float2 cph = cconj(ph);
 #pragma unroll
-        for (int k = 0; k < N; ++k) {   // A <- A G
-          const float2 ap = A[k][p], aq = A[k][q];
-          A[k][p] = cadd(cmul(ap, gpp), cmul(aq, gqp));
-          A[k][q] = cadd(cmul(ap, gpq), cmul(aq, gqq));
+        for (int k = 0; k < N; ++k) {
+          if (k == p || k == q) continue;
+          const float2 akp = A[k][p];
+          const float2 x = cmul(cph, A[k][q]);
+          const float2 nkp = make_float2(c * akp.x - s * x.x, c * akp.y - s * x.y);
+          const float2 nkq = make_float2(s * akp.x + c * x.x, s * akp.y + c * x.y);
+          A[k][p] = nkp;
+          A[p][k] = cconj(nkp);
+          A[k][q] = nkq;
+          A[q][k] = cconj(nkq);
         }
-#pragma unroll
-        for (int k = 0; k < N; ++k) {   // A <- G^H A
-          const float2 ap = A[p][k], aq = A[q][k];
-          A[p][k] = cadd(cmulc(gpp, ap), cmulc(gqp, aq));
-          A[q][k] = cadd(cmulc(gpq, ap), cmulc(gqq, aq));
-        }
+        A[p][p] = make_float2(A[p][p].x - tt * ab, 0.f);
+        A[q][q] = make_float2(A[q][q].x + tt * ab, 0.f);
         A[p][q] = make_float2(0.f, 0.f);
         A[q][p] = make_float2(0.f, 0.f);
-        A[p][p].y = 0.f;
-        A[q][q].y = 0.f;
         if (WANT_U) {
 #pragma unroll
           for (int k = 0; k < N; ++k) {   // U <- U G
-            const float2 up = U[k][p], uq = U[k][q];
-            U[k][p] = cadd(cmul(up, gpp), cmul(uq, gqp));
-            U[k][q] = cadd(cmul(up, gpq), cmul(uq, gqq));
+            const float2 up = U[k][p];
+            const float2 x = cmul(cph, U[k][q]);
+            U[k][p] = make_float2(c * up.x - s * x.x, c * up.y - s * x.y);
+            U[k][q] = make_float2(s * up.x + c * x.x, s * up.y + c * x.y);
           }
         }
       }
@@ -980,11 +983,12 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   }
   // Ritz values: eigenvalues of V^H B V of the last step (FP32)
   {
-    float2 Hh[R][R];
+    float2 Hh[R][R];   // Hermitian part of V^H B V (the Jacobi below assumes it)
 #pragma unroll
     for (int m = 0; m < R; ++m)
 #pragma unroll
-      for (int mp = 0; mp < R; ++mp) Hh[m][mp] = H[m][mp];
+      for (int mp = 0; mp < R; ++mp)
+        Hh[m][mp] = make_float2(0.5f * (H[m][mp].x + H[mp][m].x), 0.5f * (H[m][mp].y - H[mp][m].y));
     float dd[R];
     float2 UU[R][R];
     // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
