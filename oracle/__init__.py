@@ -50,9 +50,9 @@ def _load():
         lib.oracle_eigh.argtypes = [P, I, P, P]
         lib.oracle_lrkron.argtypes = [P, I, I, I, I, D, I, P, P, P, P, P, P, P, P, P]
         lib.oracle_lrkron.restype = I
-        lib.oracle_stat.argtypes = [P, P, P, I, I, I, I, P, P, I, P, P]
+        lib.oracle_stat.argtypes = [P, P, P, I, I, I, I, P, P, I, P, P, I]
         lib.oracle_kstap_cells.argtypes = [P, I, I, I, I, I, I, I, I, I, I, D, I, P, P, I, D,
-                                           P, L, P, P, P, P, P, P, P, P, P, P, P, P, I]
+                                           P, L, P, P, P, P, P, P, P, P, P, P, P, P, I, I]
         lib.oracle_kstap_cells.restype = I
         lib.oracle_num_threads.restype = I
         _lib = lib
@@ -116,16 +116,20 @@ def lrkron(S: np.ndarray, p: int, q: int, r_a: int, r_b: int, eps: float = DEFAU
     return out
 
 
+FILTERS = {"kron": 0, "classical": 1}
+
+
 def stat(X: np.ndarray, UA: np.ndarray, UB: np.ndarray, bank_a: np.ndarray,
-         bank_b: np.ndarray):
-    """Eq. KronSTAP statistic T_v for one snapshot X (p x q); returns (T, cond)."""
+         bank_b: np.ndarray, filter: str = "kron"):
+    """Statistic T_v for one snapshot X (p x q) with the Kron-STAP projector
+    (Eq. KronSTAP) or the classical one (Sec. 5); returns (T, cond)."""
     X, UA, UB, ba, bb = map(_c128, (X, UA, UB, bank_a, bank_b))
     p, q = X.shape
     V = ba.shape[0]
     T = np.zeros(V)
     cond = np.zeros(V)
     _load().oracle_stat(_ptr(X), _ptr(UA), _ptr(UB), p, q, UA.shape[1], UB.shape[1], _ptr(ba),
-                        _ptr(bb), V, _ptr(T), _ptr(cond))
+                        _ptr(bb), V, _ptr(T), _ptr(cond), FILTERS[filter])
     return T, cond
 
 
@@ -133,7 +137,8 @@ def kstap_cells(Y: np.ndarray, q: int, r_a: int, r_b: int, ring_r: int, ring_a: 
                 guard_r: int, guard_a: int, bank_a: np.ndarray, bank_b: np.ndarray, tau: float,
                 cells: Optional[np.ndarray] = None, eps: float = DEFAULT_EPS,
                 max_iter: int = DEFAULT_MAX_ITER, want_T_all: bool = True,
-                want_proj: bool = True, nthreads: int = 0) -> Dict[str, np.ndarray]:
+                want_proj: bool = True, nthreads: int = 0,
+                filter: str = "kron") -> Dict[str, np.ndarray]:
     """Whole per-cell Kron-STAP (O1-O7) on the listed cells of one frame.
 
     Y is (p, H_in, W_in) complex64; cells are flattened r * W + c indices of
@@ -162,7 +167,7 @@ def kstap_cells(Y: np.ndarray, q: int, r_a: int, r_b: int, ring_r: int, ring_a: 
         int(max_iter), _ptr(ba), _ptr(bb), V, float(tau), _ptr(cells), k, _ptr(out["T_all"]),
         _ptr(out["Tmax"]), _ptr(out["vidx"]), _ptr(out["map"]), _ptr(out["cond"]),
         _ptr(out["PA"]), _ptr(out["PB"]), _ptr(out["lamA"]), _ptr(out["lamB"]),
-        _ptr(out["gapB"]), _ptr(out["iters"]), _ptr(out["eta"]), int(nthreads))
+        _ptr(out["gapB"]), _ptr(out["iters"]), _ptr(out["eta"]), int(nthreads), FILTERS[filter])
     if rc != 0:
         raise ValueError("oracle_kstap_cells: bad arguments")
     out["cells"] = cells

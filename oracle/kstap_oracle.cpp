@@ -24,6 +24,8 @@
 //       T_v = |d_v^H P x|^2 / (d_v^H P d_v), d_v = a_v (x) b_v / sqrt(pq);
 //       T_v = 0 when d_v^H P d_v < 1e-12 |d_v|^2.
 //       Tmax = max_v T_v, vidx = lowest maximising v, map = Tmax > tau.
+//       filter = 1 selects the classical projector of Sec. 5 instead:
+//       P = I - (U_A (x) U_B)(U_A (x) U_B)^H, formed densely the same way.
 // EIG_r keeps the r algebraically largest eigenpairs (Sec. 4 definition;
 // for the PSD matrices that occur they are also the largest in magnitude).
 // Hermitian inputs to EIG are first symmetrised, herm(M) = (M + M^H)/2.
@@ -249,10 +251,12 @@ void lrkron(const std::vector<cd>& S, int p, int q, int r_a, int r_b, double eps
   for (int m = 0; m < q; ++m) res.wB_all[m] = wB[m] / sc;
 }
 
-// Dense Kron-STAP statistic (O7) for snapshot x (pq) and projector factors.
+// Dense Kron-STAP statistic (O7) for snapshot x (pq) and projector factors;
+// filter 0 = F_A (x) F_B (Eq. KronSTAP), 1 = the classical I - W W^H with
+// W = U_A (x) U_B (Sec. 5).
 void kstap_stat(const std::vector<cd>& x, const std::vector<cd>& UA, const std::vector<cd>& UB,
                 int p, int q, int r_a, int r_b, const std::vector<cd>& bank_a,
-                const std::vector<cd>& bank_b, int V, double* T, double* cond) {
+                const std::vector<cd>& bank_b, int V, double* T, double* cond, int filter) {
   const int n = p * q;
   std::vector<cd> FA((size_t)p * p), FB((size_t)q * q), P((size_t)n * n);
   for (int i = 0; i < p; ++i)
@@ -267,11 +271,29 @@ void kstap_stat(const std::vector<cd>& x, const std::vector<cd>& UA, const std::
       for (int m = 0; m < r_b; ++m) s -= UB[(size_t)i * r_b + m] * std::conj(UB[(size_t)j * r_b + m]);
       FB[(size_t)i * q + j] = s;
     }
-  for (int i = 0; i < p; ++i)  // P = FA (x) FB
-    for (int j = 0; j < q; ++j)
-      for (int k = 0; k < p; ++k)
-        for (int l = 0; l < q; ++l)
-          P[(size_t)(i * q + j) * n + (k * q + l)] = FA[(size_t)i * p + k] * FB[(size_t)j * q + l];
+  if (filter == 0) {
+    for (int i = 0; i < p; ++i)  // P = FA (x) FB
+      for (int j = 0; j < q; ++j)
+        for (int k = 0; k < p; ++k)
+          for (int l = 0; l < q; ++l)
+            P[(size_t)(i * q + j) * n + (k * q + l)] = FA[(size_t)i * p + k] * FB[(size_t)j * q + l];
+  } else {
+    // W[(i q + j), (ma r_b + mb)] = UA[i][ma] UB[j][mb];  P = I - W W^H
+    const int nw = r_a * r_b;
+    std::vector<cd> Wm((size_t)n * nw);
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < q; ++j)
+        for (int ma = 0; ma < r_a; ++ma)
+          for (int mb = 0; mb < r_b; ++mb)
+            Wm[(size_t)(i * q + j) * nw + ma * r_b + mb] =
+                UA[(size_t)i * r_a + ma] * UB[(size_t)j * r_b + mb];
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        cd s = (r == c) ? 1.0 : 0.0;
+        for (int m = 0; m < nw; ++m) s -= Wm[(size_t)r * nw + m] * std::conj(Wm[(size_t)c * nw + m]);
+        P[(size_t)r * n + c] = s;
+      }
+  }
   std::vector<cd> Px(n), d(n), Pd(n);
   for (int r = 0; r < n; ++r) {
     cd s = 0;
@@ -388,7 +410,7 @@ int oracle_lrkron(const double* S_in, int p, int q, int r_a, int r_b, double eps
 // cond (V) = d^H P d / |d|^2.
 void oracle_stat(const double* X_in, const double* UA_in, const double* UB_in, int p, int q,
                  int r_a, int r_b, const double* ba_in, const double* bb_in, int V, double* T,
-                 double* cond) {
+                 double* cond, int filter) {
   const int n = p * q;
   std::vector<cd> x(n), UA((size_t)p * r_a), UB((size_t)q * r_b), ba((size_t)V * p),
       bb((size_t)V * q);
@@ -397,7 +419,7 @@ void oracle_stat(const double* X_in, const double* UA_in, const double* UB_in, i
   for (size_t i = 0; i < UB.size(); ++i) UB[i] = cd(UB_in[2 * i], UB_in[2 * i + 1]);
   for (size_t i = 0; i < ba.size(); ++i) ba[i] = cd(ba_in[2 * i], ba_in[2 * i + 1]);
   for (size_t i = 0; i < bb.size(); ++i) bb[i] = cd(bb_in[2 * i], bb_in[2 * i + 1]);
-  kstap_stat(x, UA, UB, p, q, r_a, r_b, ba, bb, V, T, cond);
+  kstap_stat(x, UA, UB, p, q, r_a, r_b, ba, bb, V, T, cond, filter);
 }
 
 // Whole per-cell pipeline (O1-O7) over a list of cells of one frame.
@@ -415,7 +437,7 @@ int oracle_kstap_cells(const float* Y, int p, int H_in, int W_in, int q, int r_a
                        const int64_t* cells, int64_t n_cells, double* T_all, double* Tmax,
                        int32_t* vidx, uint8_t* map, double* cond, double* PA, double* PB,
                        double* lamA, double* lamB, double* gapB, int32_t* iters, double* eta,
-                       int nthreads) {
+                       int nthreads, int filter) {
   const int H = H_in - 2 * Rr;
   const int W = W_in - 2 * Ra - q + 1;
   if (p < 1 || q < 2 || H < 1 || W < 1 || r_a < 1 || r_a > p || r_b < 1 || r_b >= q || V < 1)
@@ -461,7 +483,7 @@ int oracle_kstap_cells(const float* Y, int p, int H_in, int W_in, int q, int r_a
     LRKronResult res;  // O3-O6
     lrkron(S, p, q, r_a, r_b, eps, max_iter, res);
     std::vector<double> T(V), cnd(V);  // O7
-    kstap_stat(x, res.UA, res.UB, p, q, r_a, r_b, ba, bb, V, T.data(), cnd.data());
+    kstap_stat(x, res.UA, res.UB, p, q, r_a, r_b, ba, bb, V, T.data(), cnd.data(), filter);
     double tm = -1;
     int vi = 0;
     for (int v = 0; v < V; ++v)

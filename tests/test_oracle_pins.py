@@ -240,6 +240,59 @@ def test_stat_target_orthogonal_to_clutter_gives_alpha_squared():
     assert abs(cond[v] - 1.0) < 1e-12
 
 
+def test_classical_stat_equals_projector_from_eigh_of_S():
+    """Sec. 5 classical projector: for S = A (x) B exact (rank r_a r_b), I - W W^H
+    with W = U_A (x) U_B is I minus the projector onto the leading r_a r_b
+    eigenvectors of the dense S (library eigh), so T matches that form."""
+    rng = np.random.default_rng(21)
+    p, q, V = 3, 6, 12
+    A = rand_psd(rng, p, 1)
+    B = rand_psd(rng, q, 2)
+    S = np.kron(A, B)
+    out = oracle.lrkron(S, p, q, 1, 2)
+    w, E = np.linalg.eigh(S)
+    E = E[:, -2:]
+    P = np.eye(p * q) - E @ E.conj().T
+    ba, bb = gen.steering_bank(p, q, V)
+    X = crandn(rng, p, q) * 2
+    T, cond = oracle.stat(X, out["UA"], out["UB"], ba, bb, filter="classical")
+    x = X.reshape(-1)
+    for v in range(V):
+        d = np.kron(ba[v].astype(np.complex128), bb[v].astype(np.complex128)) / np.sqrt(p * q)
+        num = abs(np.vdot(d, P @ x)) ** 2
+        den = np.vdot(d, P @ d).real
+        assert abs(T[v] - num / den) <= 1e-9 * max(1.0, num / den)
+        assert abs(cond[v] - den / np.vdot(d, d).real) <= 1e-10
+
+
+def test_classical_keeps_what_kron_removes():
+    """x = alpha d with U_B^H b = 0 but U_A^H a != 0: the classical projector
+    leaves d whole (T = |alpha|^2 |d|^2) while Kron-STAP still removes the
+    U_A direction (T = |alpha|^2 |F_A a|^2 |b|^2 / pq); and the classical
+    projector annihilates U_A (x) U_B itself."""
+    rng = np.random.default_rng(22)
+    p, q, V = 3, 8, 16
+    ba, bb = gen.steering_bank(p, q, V)
+    v = 5
+    a = ba[v].astype(np.complex128)
+    b = bb[v].astype(np.complex128)
+    UA = np.linalg.qr(crandn(rng, p, 1))[0]
+    UB = _orth_complement_basis(rng, bb[v], q, 2)
+    d = np.kron(a, b) / np.sqrt(p * q)
+    alpha = -1.5 + 2.0j
+    X = (alpha * d).reshape(p, q)
+    Tc, _ = oracle.stat(X, UA, UB, ba, bb, filter="classical")
+    Tk, _ = oracle.stat(X, UA, UB, ba, bb)
+    assert abs(Tc[v] - abs(alpha) ** 2 * np.vdot(d, d).real) < 1e-11
+    FAa = a - UA[:, 0] * np.vdot(UA[:, 0], a)
+    want = abs(alpha) ** 2 * np.vdot(FAa, FAa).real * np.vdot(b, b).real / (p * q)
+    assert abs(Tk[v] - want) < 1e-11
+    assert abs(Tc[v] - Tk[v]) > 1e-3
+    Xw = 3.0 * np.outer(UA[:, 0], UB[:, 1])          # in span(U_A (x) U_B)
+    Tw, _ = oracle.stat(Xw, UA, UB, ba, bb, filter="classical")
+    assert np.abs(Tw).max() < 1e-20
+
+
 def test_stat_matches_factored_form():
     """P = F_A (x) F_B acts on X as F_A X F_B^T, and d^H P d factorises."""
     rng = np.random.default_rng(14)
