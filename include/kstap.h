@@ -83,9 +83,15 @@ typedef struct {
    * velocities fall back to the CUDA-core arithmetic).  The tensor-core
    * route needs V <= 128.  The fit (steps 1-2) is the same for all three. */
   int precision;
+  /* Projector of the statistic: KSTAP_FILTER_KRON, F_A (x) F_B with
+   * F = I - U U^H (Eq. KronSTAP), or KSTAP_FILTER_CLASSICAL,
+   * I - (U_A (x) U_B)(U_A (x) U_B)^H, the rank r_a r_b projector that Sec. 5
+   * compares it with.  The classical filter needs precision KSTAP_FP32. */
+  int filter;
 } kstap_params;
 
 enum { KSTAP_FP32 = 0, KSTAP_FP16X3 = 1, KSTAP_BF16X3 = 2 };
+enum { KSTAP_FILTER_KRON = 0, KSTAP_FILTER_CLASSICAL = 1 };
 
 /* Per-cell LR-Kron factors, caller-owned device arrays of H * W cells each.
  *   UA    : [k][p][r_a]  complex64, orthonormal columns (U_A of Eq. KronSTAP)

@@ -32,7 +32,8 @@ class KstapParams(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("r_a", ctypes.c_int),
                 ("r_b", ctypes.c_int), ("ring_r", ctypes.c_int), ("ring_a", ctypes.c_int),
                 ("guard_r", ctypes.c_int), ("guard_a", ctypes.c_int), ("eps", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("tau", ctypes.c_float), ("precision", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("tau", ctypes.c_float), ("precision", ctypes.c_int),
+                ("filter", ctypes.c_int)]
 
 
 class KstapFactors(ctypes.Structure):
@@ -129,12 +130,13 @@ def _ptr(t) -> Optional[int]:
 
 
 PRECISION = {"fp32": 0, "fp16x3": 1, "bf16x3": 2}
+FILTER = {"kron": 0, "classical": 1}
 
 
 def make_params(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, tau, eps=0.0,
-                max_iter=0, precision="fp32") -> KstapParams:
+                max_iter=0, precision="fp32", filter="kron") -> KstapParams:
     return KstapParams(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, float(eps),
-                       int(max_iter), float(tau), PRECISION[precision])
+                       int(max_iter), float(tau), PRECISION[precision], FILTER[filter])
 
 
 def kstap_create(params: KstapParams, bank_a, bank_b, V: int, hbm_budget_bytes: int = 0,

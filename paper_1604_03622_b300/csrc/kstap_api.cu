@@ -181,6 +181,14 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "precision must be KSTAP_FP32, KSTAP_FP16X3 or KSTAP_BF16X3";
     return false;
   }
+  if (p->filter != KSTAP_FILTER_KRON && p->filter != KSTAP_FILTER_CLASSICAL) {
+    why = "filter must be KSTAP_FILTER_KRON or KSTAP_FILTER_CLASSICAL";
+    return false;
+  }
+  if (p->filter == KSTAP_FILTER_CLASSICAL && p->precision != KSTAP_FP32) {
+    why = "the classical filter runs on the KSTAP_FP32 route only";
+    return false;
+  }
   return true;
 }
 
@@ -207,6 +215,7 @@ Geom make_geom(const kstap_params& p, int V, int tc) {
   g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
   g.tau = p.tau;
   g.tc = tc > 0 ? tc : ((p.q >= 32) ? 16 : kstap::kTileCells);
+  g.filter = p.filter;
   return g;
 }
 
@@ -374,7 +383,7 @@ size_t smem_bfit(const Geom& g, bool from_store) {
 
 size_t smem_detect(const Geom& g) {
   const int P = g.p, Q = g.q, V = g.V, R = g.r_b;
-  const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 2 * (size_t)P * R;
+  const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 4 * (size_t)P * R;
   const size_t cells = cells_per_detect_block(Q);
   return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8;
 }

@@ -52,6 +52,7 @@ struct Geom {
   float eps;
   float tau;
   int tc;         // cells per tile in the B pass
+  int filter;     // 0: F_A (x) F_B (Eq. KronSTAP); 1: I - (U_A (x) U_B)(U_A (x) U_B)^H (Sec. 5)
   long long ch_stride;   // elements between channel planes of Y (>= H_in * W_in)
 };
 
@@ -1220,7 +1221,9 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   constexpr int CPW = 32 / G;                  // cells per warp
   constexpr int CPB = (kThreads / 32) * CPW;   // cells per block
   constexpr int VB = 4;                        // velocities per lane per pass
-  constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 2 * P * R;   // float2 scratch per cell
+  // float2 scratch per cell (even, so every cell's float4 blocks stay
+  // 16-byte aligned)
+  constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 4 * P * R;
   extern __shared__ __align__(16) unsigned char smem[];
   const int V = g0.V;
   float2* aT = reinterpret_cast<float2*>(smem);       // [P][V]
@@ -1253,6 +1256,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float2* Ul = Uh + Q * R;             // [Q][R]
   float2* Ua = Ul + Q * R;             // [P]   (r_a = 1)
   float4* Cs = reinterpret_cast<float4*>(Ua + 2 * P);   // [P][R] float-float complex
+  float4* Es = Cs + P * R;                               // [P][R] F_A C, float-float (classical)
   if (live) {
     const int r = (int)(cell / g.W), c = (int)(cell % g.W);
 #pragma unroll
@@ -1286,7 +1290,39 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
     }
   }
   __syncwarp();
-  // Z1 = X - C U^T (float-float) then Z = F_A Z1; lane gl owns column j = gl
+  const bool classical = g.filter == 1;
+  if (classical && live) {
+    // classical projector (W = u_a (x) U_B): d^H (I - W W^H) x splits into
+    // a^H Z1 conj(F_B b) + sum_m (a^H E[:, m]) conj(G_m), Z1 = X F_B^T,
+    // E = F_A C, G = U_B^H b.  The first term is the Kron path's product; E
+    // keeps clutter that a^H E can cancel, so E stays float-float here and
+    // a^H E is accumulated in float-float per velocity
+    for (int it = gl; it < P * R; it += G) {
+      const int i = it / R, m = it % R;
+      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;   // c_m = u_a^H C[:, m]
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        const float4 C = Cs[k2 * R + m];
+        const float2 u = Ua[k2];
+        acc_ffxf(sr, cr, C.x, C.y, u.x);
+        acc_ffxf(sr, cr, C.z, C.w, u.y);
+        acc_ffxf(si, ci, C.z, C.w, u.x);
+        acc_ffxf(si, ci, C.x, C.y, -u.y);
+      }
+      const ff cre = ff_make(sr, cr), cim = ff_make(si, ci);
+      const float4 C = Cs[i * R + m];
+      const float2 u = Ua[i];
+      float r1 = C.x, r2 = C.y, i1 = C.z, i2 = C.w;   // C[i][m] - u_a[i] c_m
+      acc_ffxf(r1, r2, cre.hi, cre.lo, -u.x);
+      acc_ffxf(r1, r2, cim.hi, cim.lo, u.y);
+      acc_ffxf(i1, i2, cim.hi, cim.lo, -u.x);
+      acc_ffxf(i1, i2, cre.hi, cre.lo, -u.y);
+      const ff er = ff_make(r1, r2), ei = ff_make(i1, i2);
+      Es[i * R + m] = make_float4(er.hi, er.lo, ei.hi, ei.lo);
+    }
+  }
+  // Z1 = X - C U^T (float-float) then Z = F_A Z1 (Kron) or Z = Z1 (classical);
+  // lane gl owns column j = gl
   if (live) {
     const int j = gl;
     float2 uh[R], ul[R];
@@ -1312,8 +1348,10 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       z[i] = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
     }
     float2 t = make_float2(0.f, 0.f);
+    if (!classical) {
 #pragma unroll
-    for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], z[i]));
+      for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], z[i]));
+    }
 #pragma unroll
     for (int i = 0; i < P; ++i) Zs[i * Q + j] = csub(z[i], cmul(Ua[i], t));
   }
@@ -1405,6 +1443,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
           dB[k] = dBn;
         }
       }
+
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
         if (base + k * G + gl >= V) break;
@@ -1418,9 +1457,29 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
         for (int i = 0; i < P; ++i) {
           const float2 wa = csub(aT[i * V + v], cmul(Ua[i], t));
           dA += cabs2(wa);
-          num = cadd(num, cmulc(wa, y[k][i]));
+          num = cadd(num, cmulc(classical ? aT[i * V + v] : wa, y[k][i]));
         }
-        const float den = dA * dB[k];
+        if (classical) {   // + sum_m (a^H E[:, m]) conj(G_m), a^H E in float-float
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              const float4 E = Es[i * R + m];
+              const float2 a = aT[i * V + v];
+              acc_ffxf(sr, cr, E.x, E.y, a.x);     // conj(a) E
+              acc_ffxf(sr, cr, E.z, E.w, a.y);
+              acc_ffxf(si, ci, E.z, E.w, a.x);
+              acc_ffxf(si, ci, E.x, E.y, -a.y);
+            }
+            num = cadd(num, cmul(make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci)),
+                                 cconj(Gm[k][m])));
+          }
+        }
+        // Kron: d^H P d = |F_A a|^2 |F_B b|^2.  Classical: |d|^2 - |W^H d|^2
+        // = |a|^2 |F_B b|^2 + |F_A a|^2 (|b|^2 - |F_B b|^2), a sum of
+        // non-negative terms (no cancellation)
+        const float den = classical ? na[v] * dB[k] + dA * fmaxf(nb[v] - dB[k], 0.f) : dA * dB[k];
         const float T = (den < 1e-12f * na[v] * nb[v]) ? 0.f : cabs2(num) / den;
         if (T_all) T_all[cell * V + v] = T;
         if (T > best) {

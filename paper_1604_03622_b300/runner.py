@@ -18,12 +18,12 @@ class KStap:
 
     def __init__(self, p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, tau, bank_a, bank_b,
                  eps=0.0, max_iter=0, hbm_budget_bytes=0, device="cuda:0", stream=None,
-                 precision="fp32"):
+                 precision="fp32", filter="kron"):
         self.dev = torch.device(device)
         self.p, self.q, self.r_a, self.r_b = p, q, r_a, r_b
         self.ring_r, self.ring_a = ring_r, ring_a
         self.params = make_params(p, q, r_a, r_b, ring_r, ring_a, guard_r, guard_a, tau, eps,
-                                  max_iter, precision)
+                                  max_iter, precision, filter)
         self.bank_a = torch.as_tensor(bank_a).to(self.dev, torch.complex64).contiguous()
         self.bank_b = torch.as_tensor(bank_b).to(self.dev, torch.complex64).contiguous()
         self.V = self.bank_a.shape[0]

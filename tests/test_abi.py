@@ -40,6 +40,8 @@ def test_create_rejects_unsupported_parameters_without_gpu():
         K.make_params(3, 16, 1, 3, 1, 7, 2, 2, 10.0),    # guard > ring
         K.make_params(3, 16, 1, 3, 0, 0, 0, 0, 10.0),    # empty ring
         K.make_params(3, 16, 1, 3, 12, 24, 1, 1, 10.0),  # box > 1024
+        K.make_params(3, 16, 1, 3, 4, 7, 1, 2, 10.0, filter="classical",
+                      precision="fp16x3"),                # classical filter: FP32 route only
     ]
     dummy = np.zeros(64, np.complex64)   # never dereferenced: validation fails first
     for prm in bad:
