@@ -200,10 +200,40 @@ def work_per_cell(wl):
     lag_per_cell = lag / tc
     m_flops = sum(q - g for g in range(q)) * NE * 8
     b_flops = sum(q - g for g in range(q)) * PP * 8
-    eig_flops = 12 * (q * q * rb * 8)            # ~12 subspace products (FP32 + FF)
+    # eigen phase: one FP32 and one float-float subspace product B V (q^2 r_b
+    # complex MACs each; >99.9 % of cells converge after one float-float
+    # step) plus the Gram and H products (2 q r_b^2 complex MACs)
+    eig_flops = 2 * (q * q * rb * 8) + 2 * (q * rb * rb * 8)
     det_flops = V * (p * q + q * rb + p) * 8 + 2 * p * q * rb * 8
+    # the B pass streams the lag sums the moments pass stored: no lag work
     return dict(frame_scale=6.0, moments=lag_per_cell + m_flops, flipflop=6 * (PP * PP * 8),
-                bfit=lag_per_cell + b_flops + eig_flops, detect=det_flops)
+                bfit=b_flops + eig_flops, detect=det_flops)
+
+
+# DRAM bytes per launch of a kernel on a workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
+# source it was taken on: the bench reports null once the file changes.
+KERNEL_SRC = os.path.join(ROOT, "paper_1604_03622_b300", "csrc", "kstap_kernels.cuh")
+TRAFFIC = {
+    # 512 x 1024-cell capture (1.263 GB read + 0.387 GB write) x 2 for the 1024^2
+    # frame: bfit's traffic is the lag store read once per position plus the
+    # per-cell a and U_B hi/lo, so it grows with the cell count
+    ("frame1024", "fp32", "bfit"): dict(
+        bytes=2 * (1.263e9 + 0.387e9),
+        sha256="8f7a20782e98f626ad6ca34eaafb5b208654fc7d5acfd2bb8e200ee1d2c48f95",
+        source="profiles/frame1024_512x1024_kernels.md"),
+}
+
+
+def measured_traffic(workload: str, precision: str, kernel: str):
+    import hashlib
+    t = TRAFFIC.get((workload, precision, kernel))
+    if t is None:
+        return None, None
+    with open(KERNEL_SRC, "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != t["sha256"]:
+            return None, "kernel source changed since the capture"
+    return t["bytes"], t["source"]
 
 
 # ------------------------------------------------------- batched vs plain ---
@@ -463,12 +493,13 @@ def main():
     dom_ms, dom_n = kt[dom]
     per_launch_ms = dom_ms / max(dom_n, 1)
     achieved = work[dom] * ncell / (per_launch_ms / 1e3) / 1e12
+    traffic_bytes, traffic_src = measured_traffic(wl.name, args.precision, dom)
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
     peak_clock = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FP32 FMA: 128 lanes/SM
     peak_max = 148 * 128 * 2 * 2032e6 / 1e12
     roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak_max, unit="TFLOP/s",
                 frac=achieved / peak_max, frac_at_measured_clock=achieved / peak_clock,
-                traffic=None,
+                traffic=traffic_bytes, traffic_source=traffic_src,
                 peak_note="148 SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock); "
                           "no measured FP32 peak in MEASURED_PEAKS.json",
                 kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()},
