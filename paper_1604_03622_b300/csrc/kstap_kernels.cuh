@@ -320,6 +320,7 @@ __device__ __forceinline__ void ll_to_ff(long long v, float& hi, float& lo) {
 
 constexpr int kMomRows = 4;                         // cell rows per CTA in the moments pass
 constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
+constexpr int kHChunk = 3;                          // positions per item in the running ring sums
 
 // ------------------------------------------------ K1a: lag moments ---------
 // CTA = kMomRows cell rows x kTileCells cells, one thread per cell.  The
@@ -395,65 +396,95 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
   for (int lagg = Q - 1; lagg >= 0; --lagg) {
     const int NU = TC + Q - 1 - lagg;
     const int KW = NU + 2 * g.Ra;
+    const bool last_tile = c0 + TC >= g.W;
+    const int WL = g.W + Q - 1;
+    const int nch = (NU + kHChunk - 1) / kHChunk;
+#pragma unroll 1
     for (int t = 0; t < TR; ++t) {
-      // vertical ring sums of cell row t: direct for t = 0, running after
-      for (int idx = threadIdx.x; idx < PP * KW; idx += blockDim.x) {
-        const int kap = idx % KW, J = idx / KW;
-        const int i = J % P, k = J / P;
-        const int2* yi = Yq + (size_t)i * NRT * WT + kap;
-        const int2* yk = Yq + (size_t)k * NRT * WT + kap + lagg;
-        auto prod = [&](int rho, long long& pr, long long& pim) {
-          const int2 a = yi[rho * WT], b = yk[rho * WT];
-          pr = (long long)a.x * b.x + (long long)a.y * b.y;
-          pim = (long long)a.y * b.x - (long long)a.x * b.y;
-        };
-        long long pr, pim;
-        longlong2 vo, vg;
+      // (1) vertical ring sums of cell row t, one item per (channel i, column
+      // kap) covering the P pairs J = i + P k (one load of channel i per row
+      // serves them all): direct for t = 0, running (rows entering and leaving
+      // the box and the guard band) after
+      for (int item = threadIdx.x; item < P * KW; item += blockDim.x) {
+        const int i = item / KW, kap = item - i * KW;
         if (t == 0) {
-          vo = make_longlong2(0, 0);
-          vg = make_longlong2(0, 0);
+          longlong2 vo[P], vg[P];
+#pragma unroll
+          for (int k = 0; k < P; ++k) vo[k] = vg[k] = make_longlong2(0, 0);
           for (int rho = 0; rho < NR; ++rho) {
-            prod(rho, pr, pim);
-            vo.x += pr;
-            vo.y += pim;
-            if (rho >= g0 && rho <= g1) {
-              vg.x += pr;
-              vg.y += pim;
+            const int2 a = Yq[(i * NRT + rho) * WT + kap];
+            const bool guard = rho >= g0 && rho <= g1;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+              const int2 b = Yq[(k * NRT + rho) * WT + kap + lagg];
+              const long long pr = (long long)a.x * b.x + (long long)a.y * b.y;
+              const long long pim = (long long)a.y * b.x - (long long)a.x * b.y;
+              vo[k].x += pr;
+              vo[k].y += pim;
+              if (guard) {
+                vg[k].x += pr;
+                vg[k].y += pim;
+              }
             }
           }
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            Vo[(i + P * k) * WT + kap] = vo[k];
+            Vg[(i + P * k) * WT + kap] = vg[k];
+          }
         } else {
-          vo = Vo[J * KW + kap];
-          vg = Vg[J * KW + kap];
-          prod(t - 1 + NR, pr, pim);
-          vo.x += pr;
-          vo.y += pim;
-          prod(t - 1, pr, pim);
-          vo.x -= pr;
-          vo.y -= pim;
-          prod(t + g1, pr, pim);
-          vg.x += pr;
-          vg.y += pim;
-          prod(t - 1 + g0, pr, pim);
-          vg.x -= pr;
-          vg.y -= pim;
+          const int2 ai = Yq[(i * NRT + t - 1 + NR) * WT + kap];   // entering the box
+          const int2 ao = Yq[(i * NRT + t - 1) * WT + kap];        // leaving it
+          const int2 gi = Yq[(i * NRT + t + g1) * WT + kap];       // entering the guard band
+          const int2 go = Yq[(i * NRT + t - 1 + g0) * WT + kap];   // leaving it
+#pragma unroll 1
+          for (int k = 0; k < P; ++k) {
+            const int J = i + P * k;
+            const int2* yk = Yq + (size_t)k * NRT * WT + kap + lagg;
+            const int2 bi = yk[(t - 1 + NR) * WT], bo = yk[(t - 1) * WT];
+            const int2 hi = yk[(t + g1) * WT], ho = yk[(t - 1 + g0) * WT];
+            longlong2 vo = Vo[J * WT + kap], vg = Vg[J * WT + kap];
+            vo.x += (long long)ai.x * bi.x + (long long)ai.y * bi.y -
+                    (long long)ao.x * bo.x - (long long)ao.y * bo.y;
+            vo.y += (long long)ai.y * bi.x - (long long)ai.x * bi.y -
+                    (long long)ao.y * bo.x + (long long)ao.x * bo.y;
+            vg.x += (long long)gi.x * hi.x + (long long)gi.y * hi.y -
+                    (long long)go.x * ho.x - (long long)go.y * ho.y;
+            vg.y += (long long)gi.y * hi.x - (long long)gi.x * hi.y -
+                    (long long)go.y * ho.x + (long long)go.x * ho.y;
+            Vo[J * WT + kap] = vo;
+            Vg[J * WT + kap] = vg;
+          }
         }
-        Vo[J * KW + kap] = vo;
-        Vg[J * KW + kap] = vg;
       }
       __syncthreads();
-      // horizontal ring sums, one thread per (plane, position): consecutive
-      // threads read consecutive shared-memory words
-      const bool last_tile = c0 + TC >= g.W;
-      const int WL = g.W + Q - 1;
-      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
-        const int u = idx % NU, J = idx / NU;
-        const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
-        float4 v;
-        ll_to_ff(L.x, v.x, v.y);
-        ll_to_ff(L.y, v.z, v.w);
-        lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
-        if (Lw && (u < TC || last_tile) && c0 + u < WL && r0 + t < g.H)
-          Lw[(((size_t)(r0 + t) * Q + lagg) * PP + J) * WL + c0 + u] = v;
+      // (2) horizontal ring sums, exact int64, one item per (plane, chunk of
+      // kHChunk positions): the chunk's first sum direct, the rest running
+      // (L(u + 1) = L(u) + Vo[u + 1 + 2Ra] - Vo[u] - Vg[u + 1 + Ra + Ga] +
+      // Vg[u + Ra - Ga]); kHChunk is odd, so the lanes of a warp start in
+      // different 16-byte bank groups.  Each sum goes straight to
+      // float-float: row t's hi parts for the M products, and the lag store
+      // (positions of this tile; the last tile also its halo).
+      for (int item = threadIdx.x; item < PP * nch; item += blockDim.x) {
+        const int J = item / nch, u0 = (item - J * nch) * kHChunk;
+        const int u1 = min(u0 + kHChunk, NU);
+        const longlong2* vo = Vo + J * WT;
+        const longlong2* vg = Vg + J * WT;
+        longlong2 L = ring_sum(vo, vg, g, u0);
+        for (int u = u0; u < u1; ++u) {
+          if (u > u0) {
+            const longlong2 a = vo[u + 2 * g.Ra], b = vo[u - 1];
+            const longlong2 c = vg[u + g.Ra + g.Ga], d = vg[u - 1 + g.Ra - g.Ga];
+            L.x += a.x - b.x - c.x + d.x;
+            L.y += a.y - b.y - c.y + d.y;
+          }
+          float4 v;
+          ll_to_ff(L.x, v.x, v.y);
+          ll_to_ff(L.y, v.z, v.w);
+          lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
+          if (Lw && (u < TC || last_tile) && c0 + u < WL && r0 + t < g.H)
+            Lw[(((size_t)(r0 + t) * Q + lagg) * PP + J) * WL + c0 + u] = v;
+        }
       }
       __syncthreads();
     }
