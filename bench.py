@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    ap.add_argument("--no-precision-leg", action="store_true",
+                    help="skip the 2048^2 q = 32 frame (FP32 and FP16X3 banks)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg on the 256-tile workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -310,6 +312,48 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
                 speedup=pm / bm, tuning=tuning)
 
 
+# --------------------------------------------------------- q = 32 frame ---
+def precision_leg(dev, steps: int, warmup: int):
+    """The 2048 x 2048-cell q = 32 frame (p = 3, r_b = 4, n = 192, V = 128,
+    40 dB CNR): plain path, per-step CUDA events with an L2 flush between
+    steps, once with the FP32 bank and once with the FP16X3 tensor-core bank;
+    per-kernel times from the library's events."""
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    wl = gen.WORKLOADS["precision2048"]
+    f = gen.make_frame(wl)
+    Y = torch.from_numpy(f.Y).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = dict(workload=wl.name, cells_per_frame=wl.cells, q=wl.q, r_b=wl.r_b, n=wl.n, V=wl.V)
+    for prec in ("fp32", "fp16x3"):
+        ks = KStap.from_workload(wl, f.bank_a, f.bank_b, device=str(dev), stream=stream,
+                                 precision=prec)
+        for _ in range(warmup):
+            ks.run(Y)
+        torch.cuda.synchronize(dev)
+        K.kstap_set_profiling(ks.ctx, True)
+        ms = []
+        for s in range(steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ks.run(Y)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        kt = K.kstap_kernel_times(ks.ctx)
+        ks.close()
+        out[prec] = dict(cells_per_s=wl.cells * len(ms) / (sum(ms) / 1e3),
+                         ms_per_frame=sum(ms) / len(ms), p99_ms=sorted(ms)[-1],
+                         kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()})
+    del Y, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- serving ---
 def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
     """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
@@ -511,6 +555,8 @@ def main():
 
     serving = None if args.no_serving else serving_leg(dev, args.serve_requests)
 
+    precision = None if args.no_precision_leg else precision_leg(dev, 3, 3)
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -540,7 +586,7 @@ def main():
                                           ms_per_step=e2e_total / args.steps),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
-        batched=batched, serving=serving)
+        batched=batched, serving=serving, precision_q32=precision)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:
