@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    ap.add_argument("--no-paper-timing", action="store_true",
+                    help="skip the single large-covariance LR-Kron timing grid")
     ap.add_argument("--no-precision-leg", action="store_true",
                     help="skip the 2048^2 q = 32 frame (FP32 and FP16X3 banks)")
     ap.add_argument("--no-batched", action="store_true",
@@ -354,6 +356,50 @@ def precision_leg(dev, steps: int, warmup: int):
     return out
 
 
+# ------------------------------------------- paper's LR-Kron timing workload ---
+def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
+    """One large-covariance LR-Kron fit (Sec. 7.1: rank-one A, B = I, n = 5) for
+    p = 3, q in {50, 250, 1000, 2500} and p = 6, q in {25, 125, 500, 1250}, at
+    eps = 1e-4 and 1e-6: kstap_lrkron_fit timed with CUDA events (median of
+    `reps` after a warm-up, snapshots resident on the device), and the FP64
+    oracle (dense S, literal Alg. 1 and Alg. 2) on the host cores for the two
+    smallest q of each p."""
+    import torch
+    import gen
+    import oracle
+    import paper_1604_03622_b300 as K
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for p, qs in ((3, (50, 250, 1000, 2500)), (6, (25, 125, 500, 1250))):
+        for q in qs:
+            X = gen.lrkron_timing_case(p, q)
+            Xd = torch.from_numpy(X).to(dev)
+            A = torch.empty(p, p, dtype=torch.complex64, device=dev)
+            B = torch.empty(q, q, dtype=torch.complex64, device=dev)
+            for eps in (1e-4, 1e-6):
+                K.kstap_lrkron_fit(Xd, 1, eps, 100, A, B, stream.cuda_stream)
+                ms = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    _, _, it, eta = K.kstap_lrkron_fit(Xd, 1, eps, 100, A, B, stream.cuda_stream)
+                    b.record(stream)
+                    b.synchronize()
+                    ms.append(a.elapsed_time(b))
+                row = dict(p=p, q=q, n=X.shape[0], eps=eps, iters=it, eta=eta,
+                           gpu_ms=statistics.median(ms))
+                if cpu and q <= (250 if p == 3 else 125):
+                    x = np.stack([X[m].reshape(-1) for m in range(X.shape[0])]).astype(np.complex128)
+                    t0 = time.perf_counter()
+                    S = (x.T @ x.conj()) / X.shape[0]
+                    oracle.lrkron(S, p, q, 1, q, eps=eps, max_iter=100)
+                    row["cpu_oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+                rows.append(row)
+            del Xd, A, B
+    return dict(workload="single large-covariance LR-Kron (Sec. 7.1)", rows=rows,
+                cpu_cores=__import__("oracle").num_threads())
+
+
 # ----------------------------------------------------------------- serving ---
 def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
     """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
@@ -557,6 +603,9 @@ def main():
 
     precision = None if args.no_precision_leg else precision_leg(dev, 3, 3)
 
+    paper_timing = None if args.no_paper_timing else paper_timing_leg(
+        dev, cpu=not args.no_cpu_baseline)
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -586,7 +635,7 @@ def main():
                                           ms_per_step=e2e_total / args.steps),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
-        batched=batched, serving=serving, precision_q32=precision)
+        batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

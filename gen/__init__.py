@@ -266,3 +266,21 @@ def poisson_arrivals(n: int, rate_hz: float, n_frames: int, seed: int = SEED_BAS
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
     idx = rng.integers(0, n_frames, size=n)
     return t, idx
+
+
+def lrkron_timing_case(p: int, q: int, n: int = 5, sigma2: float = 0.1,
+                       seed: int = SEED_BASE + 6) -> np.ndarray:
+    """Snapshots of the single large-covariance LR-Kron timing workload (Sec. 7.1):
+    x_m = vec(X_m^T) ~ CN(0, A (x) I_q + sigma2 I_pq), m < n, with A = u u^H a
+    random complex rank-one p x p matrix (|u| = 1) and B = I_q.  Returns
+    X (n, p, q) complex64.  sigma2 = 0 gives the noiseless model, whose sample
+    covariance is exactly separable."""
+    rng = np.random.default_rng([seed, STREAM_CLUTTER])
+    u = _cn(rng, p)
+    u = u / np.linalg.norm(u)
+    w = _cn(rng, (n, q))                                  # B = I: white temporal factor
+    X = u[None, :, None] * w[:, None, :]                  # X_m = u w_m^T
+    if sigma2 > 0:
+        rng_n = np.random.default_rng([seed, STREAM_NOISE])
+        X = X + np.sqrt(sigma2) * _cn(rng_n, (n, p, q))
+    return np.ascontiguousarray(X.astype(np.complex64))

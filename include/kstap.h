@@ -307,6 +307,26 @@ kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket);
 kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y, int H_in,
                                        int W_in, const kstap_factors* factors, void* cuda_stream);
 
+/* One large-covariance LR-Kron fit (Alg. 2), the paper's timing workload
+ * (Sec. 7.1): S = (1/n) sum_m x_m x_m^H from n snapshots x_m = vec(X_m^T),
+ * fitted as A (x) B with rank(A) <= r_a and B untruncated (r_b = q, as in
+ * that experiment), Alg. 2 from A_0 = vec^-1(R 1 / q^2), stopping when
+ * |eta_k - eta_k-1| <= eps (eps <= 0 selects 1e-6) or after max_iter
+ * iterations (<= 0 selects 100).  R = R(S) is never formed: every step is
+ * evaluated through the n^2 p x p Grams X_m X_m'^H (FP64).
+ *   X     : device, n x p x q complex64, X[m][i][j] (channel i, pulse j)
+ *   A_out : device, p x p complex64 row-major, A^ with tr A^ = p (may be NULL)
+ *   B_out : device, q x q complex64 row-major, B^ = vec^-1(b) of the last b
+ *           (scaled by the same normalisation), Hermitian
+ *   iters, eta (host, may be NULL): iterations taken and the final
+ *           |R - a b^T|_F / |R|_F
+ * Limits: 1 <= n <= 16, 1 <= p <= 8, 2 <= q <= 16384, 1 <= r_a <= p.  Needs no
+ * context; allocates its ~KB of scratch stream-ordered on cuda_stream and
+ * synchronises that stream before returning.  Errors: kstap_last_error(NULL). */
+kstap_status kstap_lrkron_fit(const kstap_c64* X, int n, int p, int q, int r_a, double eps,
+                              int max_iter, kstap_c64* A_out, kstap_c64* B_out, int32_t* iters,
+                              double* eta, void* cuda_stream);
+
 /* Bytes of workspace kstap_fit_project needs for an H_in x W_in frame with
  * these parameters (0 on invalid input). */
 size_t kstap_workspace_bytes(const kstap_params* params, int H_in, int W_in);

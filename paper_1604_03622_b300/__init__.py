@@ -24,7 +24,7 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
-            "kstap_release", "kstap_fit_report", "kstap_device_status"]
+            "kstap_release", "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
 
 
@@ -104,6 +104,9 @@ def lib() -> ctypes.CDLL:
         L.kstap_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KstapResult), I]
         L.kstap_release.argtypes = [P, ctypes.c_uint64]
         L.kstap_device_status.argtypes = [P]
+        L.kstap_lrkron_fit.argtypes = [P, I, I, I, I, ctypes.c_double, I, P, P,
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_double), P]
         L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]
         L.kstap_set_profiling.argtypes = [P, I]
@@ -113,7 +116,7 @@ def lib() -> ctypes.CDLL:
                      "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
                      "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
-                     "kstap_fit_report", "kstap_device_status"):
+                     "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -165,6 +168,23 @@ def kstap_fit_report(ctx: int):
     if st != KSTAP_WARN_NOCONV:
         _check(st, ctx)
     return int(nc.value), int(nf.value)
+
+
+def kstap_lrkron_fit(X, r_a: int = 1, eps: float = 1e-6, max_iter: int = 100, A_out=None,
+                     B_out=None, stream: int = 0):
+    """One large-covariance LR-Kron fit from snapshots X (n, p, q) complex64 on
+    the device.  A_out (p, p) and B_out (q, q) are complex64 device tensors
+    (allocated with torch when None).  Returns (A_out, B_out, iters, eta)."""
+    import torch
+    n, p, q = X.shape
+    if A_out is None:
+        A_out = torch.empty(p, p, dtype=torch.complex64, device=X.device)
+    if B_out is None:
+        B_out = torch.empty(q, q, dtype=torch.complex64, device=X.device)
+    it, et = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().kstap_lrkron_fit(_ptr(X), n, p, q, r_a, float(eps), int(max_iter), _ptr(A_out),
+                                  _ptr(B_out), ctypes.byref(it), ctypes.byref(et), stream or None))
+    return A_out, B_out, int(it.value), float(et.value)
 
 
 def kstap_device_status(ctx: int) -> None:

@@ -23,6 +23,7 @@
 #include "../../include/kstap.h"
 #include "kstap_kernels.cuh"
 #include "kstap_tc.cuh"
+#include "kstap_lrk.cuh"
 
 using kstap::Geom;
 using kstap::Job;
@@ -1549,4 +1550,60 @@ extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, co
   fill_jobs(*params, g, fr, (char*)scratch, &L, jobs, JL);
   return dispatch_fit(nullptr, nullptr, g, JL, (char*)scratch, L, false, sms > 0 ? sms : 148, 4,
                       (cudaStream_t)cuda_stream);
+}
+
+// ------------------------------------------------ large-covariance fit -----
+extern "C" kstap_status kstap_lrkron_fit(const kstap_c64* X, int n, int p, int q, int r_a,
+                                         double eps, int max_iter, kstap_c64* A_out,
+                                         kstap_c64* B_out, int32_t* iters, double* eta,
+                                         void* cuda_stream) {
+  if (!X || !B_out) return fail(nullptr, KSTAP_EINVAL, "X and B_out are required");
+  if (n < 1 || n > kstap::kLrkMaxN || p < 1 || p > kstap::kLrkMaxP || q < 2 || q > 16384 ||
+      r_a < 1 || r_a > p)
+    return fail(nullptr, KSTAP_EINVAL,
+                "need 1 <= n <= %d, 1 <= p <= %d, 2 <= q <= 16384, 1 <= r_a <= p",
+                kstap::kLrkMaxN, kstap::kLrkMaxP);
+  if (!(eps > 0.0)) eps = 1e-6;
+  if (max_iter < 1) max_iter = 100;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int np = n * p, p2 = p * p;
+  const size_t nG = (size_t)np * np, nT = (size_t)p2 * p2;
+  const size_t bytes = (nG + np + nT + 2 * (size_t)p2) * sizeof(double2) + 8 * sizeof(double);
+  char* ws = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&ws, bytes, st);
+  if (e != cudaSuccess)
+    return fail(nullptr, KSTAP_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  double2* G = (double2*)ws;
+  double2* s = G + nG;
+  double2* Tm = s + np;
+  double2* Afin = Tm + nT;
+  double2* Aprev = Afin + p2;
+  double* info = (double*)(Aprev + p2);
+  kstap_status res = KSTAP_OK;
+  const size_t smem = 2 * (size_t)np * kstap::kLrkTile * sizeof(float2);
+  double hinfo[5] = {0, 0, 0, 0, 0};
+  do {
+    kstap::k_lrk_gram<<<dim3(np, np + 1), 256, 0, st>>>((const float2*)X, np, q, G, s);
+    kstap::k_lrk_tmat<<<(unsigned)((nT + 127) / 128), 128, 0, st>>>(G, n, p, Tm);
+    kstap::k_lrk_iterate<<<1, 32, 0, st>>>(Tm, G, s, n, p, q, r_a, eps, max_iter, Afin, Aprev,
+                                           info);
+    if (A_out) kstap::k_lrk_aout<<<1, 64, 0, st>>>(Afin, info, p, (float2*)A_out);
+    if ((e = cudaFuncSetAttribute(kstap::k_lrk_bout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      break;
+    const unsigned nt = (unsigned)((q + kstap::kLrkTile - 1) / kstap::kLrkTile);
+    kstap::k_lrk_bout<<<dim3(nt, nt), 256, smem, st>>>((const float2*)X, Aprev, info, n, p, q,
+                                                       (float2*)B_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      break;
+  } while (0);
+  cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return fail(nullptr, KSTAP_ECUDA, "kstap_lrkron_fit: %s", cudaGetErrorString(e));
+  if (iters) *iters = (int32_t)hinfo[3];
+  if (eta) *eta = hinfo[2];
+  return res;
 }

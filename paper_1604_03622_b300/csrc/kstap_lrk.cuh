@@ -1,0 +1,308 @@
+// One large-covariance LR-Kron fit (Alg. 2) from n snapshots X_m (p x q):
+// the paper's timing workload (Sec. 7.1: rank-one A, B = I so r_b = q, n = 5,
+// q up to 2500).  R = R(S) (p^2 x q^2, Alg. 1) is never formed.  With
+// G_mm' = X_m X_m'^H (p x p) every quantity of Alg. 2 is a small expression:
+//   B   = vec^-1(b) = (1 / (n |a|^2)) sum_m X_m^T conj(A) conj(X_m)      (q x q)
+//   |b|^2 = Re <A, T(A)> / (n^2 |a|^2^2),  T(A) = sum_mm' G_mm' A G_m'm
+//   A~  = vec^-1(R conj(b) / |b|^2) = T(A) / (n^2 |a|^2 |b|^2)
+//   |R|^2 = |S|_F^2 = sum_mm' |tr G_m'm|^2 / n^2
+//   A_0 = vec^-1(R 1 / q^2) = sum_m s_m s_m^H / (n q^2),  s_m = X_m 1
+//   eta^2 = (|R|^2 - 2 |b|^2 Re <a', a~> + |a'|^2 |b|^2) / |R|^2
+// T is linear in A: vec(T(A)) = Tm vec(A) with the p^2 x p^2 matrix
+// Tm = sum_mm' G_m'm^T (x) G_mm' (vec column-major, a[i + p k] = A[i][k]).
+// The Grams and the iteration run in FP64 (the loop test |eta_k - eta_k-1|
+// <= eps resolves differences of 1e-6 and below); only B^, the one q x q
+// output, is formed, in FP32 by a tiled kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kstap {
+
+constexpr int kLrkMaxP = 8;
+constexpr int kLrkMaxN = 16;
+
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Block-wide FP64 sum over blockDim.x (a multiple of 32, <= 1024) threads.
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < nw; ++k) t += red[k];   // same order in every thread
+  return t;
+}
+
+// Grid (n p, n p + 1): block (r1, r2) forms sum_j X_r1[j] conj(X_r2[j]) over
+// the rows r = m p + i of X (n p rows of q), i.e. G_big[r1][r2] with
+// G_mm'[i][k] = G_big[m p + i][m' p + k]; column n p gives the row sums s_r1.
+__global__ void k_lrk_gram(const float2* __restrict__ X, int np, int q, double2* __restrict__ G,
+                           double2* __restrict__ s) {
+  __shared__ double red[32];
+  const int r1 = blockIdx.x, r2 = blockIdx.y;
+  const bool ones = r2 == np;
+  const float2* x1 = X + (size_t)r1 * q;
+  const float2* x2 = X + (size_t)(ones ? r1 : r2) * q;
+  double sr = 0.0, si = 0.0;
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    const float2 a = x1[j];
+    if (ones) {
+      sr += a.x;
+      si += a.y;
+    } else {
+      const float2 b = x2[j];
+      sr += (double)a.x * b.x + (double)a.y * b.y;
+      si += (double)a.y * b.x - (double)a.x * b.y;
+    }
+  }
+  sr = block_sum_d(sr, red);
+  si = block_sum_d(si, red);
+  if (threadIdx.x == 0) {
+    if (ones)
+      s[r1] = make_double2(sr, si);
+    else
+      G[(size_t)r1 * np + r2] = make_double2(sr, si);
+  }
+}
+
+// Tm[(i + p k)][(i2 + p k2)] = sum_mm' G_m'm[k2][k] G_mm'[i][i2]; one thread
+// per entry (p^4 of them).
+__global__ void k_lrk_tmat(const double2* __restrict__ G, int n, int p, double2* __restrict__ Tm) {
+  const int p2 = p * p, np = n * p;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p2 * p2) return;
+  const int row = e / p2, col = e % p2;
+  const int i = row % p, k = row / p, i2 = col % p, k2 = col / p;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int m = 0; m < n; ++m)
+    for (int mp = 0; mp < n; ++mp) {
+      const double2 g1 = G[(size_t)(mp * p + k2) * np + (m * p + k)];   // G_m'm[k2][k]
+      const double2 g2 = G[(size_t)(m * p + i) * np + (mp * p + i2)];   // G_mm'[i][i2]
+      acc = zadd(acc, zmul(g1, g2));
+    }
+  Tm[e] = acc;
+}
+
+// Cyclic Jacobi on a Hermitian p x p matrix (FP64, row-major in `A`); on
+// return w holds the eigenvalues in decreasing order and the columns of U
+// (row-major) the eigenvectors.
+__device__ void lrk_jacobi(double2* A, int p, double* w, double2* U) {
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) U[i * p + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < p; ++i) {
+      diag += A[i * p + i].x * A[i * p + i].x;
+      for (int j = i + 1; j < p; ++j) off += zabs2(A[i * p + j]);
+    }
+    if (off <= 1e-30 * diag || off == 0.0) break;
+    for (int a = 0; a < p - 1; ++a)
+      for (int b = a + 1; b < p; ++b) {
+        const double2 apq = A[a * p + b];
+        const double ab = sqrt(zabs2(apq));
+        if (ab == 0.0) continue;
+        const double2 ph = make_double2(apq.x / ab, apq.y / ab);
+        const double tau = (A[b * p + b].x - A[a * p + a].x) / (2.0 * ab);
+        const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        const double2 cph = zconj(ph);
+        for (int k = 0; k < p; ++k) {
+          if (k == a || k == b) continue;
+          const double2 akp = A[k * p + a];
+          const double2 x = zmul(cph, A[k * p + b]);
+          const double2 nkp = make_double2(c * akp.x - sn * x.x, c * akp.y - sn * x.y);
+          const double2 nkq = make_double2(sn * akp.x + c * x.x, sn * akp.y + c * x.y);
+          A[k * p + a] = nkp;
+          A[a * p + k] = zconj(nkp);
+          A[k * p + b] = nkq;
+          A[b * p + k] = zconj(nkq);
+        }
+        A[a * p + a] = make_double2(A[a * p + a].x - t * ab, 0.0);
+        A[b * p + b] = make_double2(A[b * p + b].x + t * ab, 0.0);
+        A[a * p + b] = make_double2(0.0, 0.0);
+        A[b * p + a] = make_double2(0.0, 0.0);
+        for (int k = 0; k < p; ++k) {
+          const double2 up = U[k * p + a];
+          const double2 x = zmul(cph, U[k * p + b]);
+          U[k * p + a] = make_double2(c * up.x - sn * x.x, c * up.y - sn * x.y);
+          U[k * p + b] = make_double2(sn * up.x + c * x.x, sn * up.y + c * x.y);
+        }
+      }
+  }
+  for (int i = 0; i < p; ++i) w[i] = A[i * p + i].x;
+  for (int i = 0; i < p - 1; ++i)
+    for (int j = i + 1; j < p; ++j)
+      if (w[j] > w[i]) {
+        const double tw = w[i];
+        w[i] = w[j];
+        w[j] = tw;
+        for (int k = 0; k < p; ++k) {
+          const double2 u = U[k * p + i];
+          U[k * p + i] = U[k * p + j];
+          U[k * p + j] = u;
+        }
+      }
+}
+
+// A^ = sc vec^-1(a_fin) (row-major complex64 output), sc = p / tr.
+__global__ void k_lrk_aout(const double2* __restrict__ A_fin, const double* __restrict__ info,
+                           int p, float2* __restrict__ Aout) {
+  const int e = threadIdx.x;
+  if (e >= p * p) return;
+  const double sc = (info[1] != 0.0) ? (double)p / info[1] : 1.0;
+  const int i = e / p, k = e % p;
+  const double2 v = A_fin[i + p * k];
+  Aout[e] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+}
+
+// Alg. 2 on the p^2 x p^2 operator Tm: one warp, FP64.  Writes the final a
+// (vec, column-major) to A_fin, the a that produced the last b to A_prev, and
+// info = {|a_prev|^2, tr A_fin, eta, iterations, |R|^2}.
+__global__ void k_lrk_iterate(const double2* __restrict__ Tm, const double2* __restrict__ G,
+                              const double2* __restrict__ s, int n, int p, int q, int r_a,
+                              double eps, int max_iter, double2* __restrict__ A_fin,
+                              double2* __restrict__ A_prev, double* __restrict__ info) {
+  constexpr int PP = kLrkMaxP * kLrkMaxP;
+  __shared__ double2 a[PP], t[PP], Am[PP], U[PP];
+  __shared__ double w[kLrkMaxP];
+  __shared__ int done;
+  const int lane = threadIdx.x, p2 = p * p, np = n * p;
+  double Rn2 = 0.0;
+  if (lane == 0) {
+    for (int m = 0; m < n; ++m)       // |R|^2 = sum_mm' |tr G_m'm|^2 / n^2
+      for (int mp = 0; mp < n; ++mp) {
+        double2 tr = make_double2(0.0, 0.0);
+        for (int i = 0; i < p; ++i) tr = zadd(tr, G[(size_t)(mp * p + i) * np + (m * p + i)]);
+        Rn2 += zabs2(tr);
+      }
+    Rn2 /= (double)n * n;
+    for (int i = 0; i < p; ++i)       // A_0[i][k] = sum_m s_m[i] conj(s_m[k]) / (n q^2)
+      for (int k = 0; k < p; ++k) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < n; ++m) acc = zadd(acc, zmul(s[m * p + i], zconj(s[m * p + k])));
+        a[i + p * k] = make_double2(acc.x / ((double)n * q * q), acc.y / ((double)n * q * q));
+      }
+    done = 0;
+  }
+  __syncwarp();
+  double eta_prev = 1.0 / 0.0, an_prev = 0.0, eta = 0.0;
+  int it = 0;
+  while (true) {
+    for (int r = lane; r < p2; r += 32) {   // t = Tm vec(A)
+      double2 acc = make_double2(0.0, 0.0);
+      for (int c = 0; c < p2; ++c) acc = zadd(acc, zmul(Tm[(size_t)r * p2 + c], a[c]));
+      t[r] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double an = 0.0, ip = 0.0;
+      for (int J = 0; J < p2; ++J) {
+        an += zabs2(a[J]);
+        ip += a[J].x * t[J].x + a[J].y * t[J].y;   // Re <A, T(A)>
+      }
+      const double nn = (double)n * n;
+      const double bn = (an > 0.0) ? ip / (nn * an * an) : 0.0;
+      if (!(an > 0.0) || !(bn > 0.0)) {
+        done = 1;
+      } else {
+        const double f = 1.0 / (nn * an * bn);
+        for (int i = 0; i < p; ++i)        // herm(vec^-1 a~), row-major
+          for (int k = 0; k < p; ++k) {
+            const double2 x = t[i + p * k], y = t[k + p * i];
+            Am[i * p + k] = make_double2(0.5 * f * (x.x + y.x), 0.5 * f * (x.y - y.y));
+          }
+        lrk_jacobi(Am, p, w, U);
+        double anew = 0.0, re = 0.0;
+        for (int i = 0; i < p; ++i)
+          for (int k = 0; k < p; ++k) {
+            double2 acc = make_double2(0.0, 0.0);   // EIG_{r_a}: sum_m w_m u_m u_m^H
+            for (int m = 0; m < r_a; ++m) {
+              const double2 uu = zmul(U[i * p + m], zconj(U[k * p + m]));
+              acc = make_double2(acc.x + w[m] * uu.x, acc.y + w[m] * uu.y);
+            }
+            const double2 at = make_double2(f * t[i + p * k].x, f * t[i + p * k].y);   // a~
+            anew += zabs2(acc);
+            re += acc.x * at.x + acc.y * at.y;                                         // Re <a', a~>
+            A_prev[i + p * k] = a[i + p * k];
+            a[i + p * k] = acc;
+          }
+        an_prev = an;
+        const double e2 = (Rn2 > 0.0) ? (Rn2 - 2.0 * bn * re + anew * bn) / Rn2 : 0.0;
+        eta = sqrt(e2 > 0.0 ? e2 : 0.0);
+        ++it;
+        done = (fabs(eta - eta_prev) <= eps) || (it >= max_iter);
+        eta_prev = eta;
+      }
+    }
+    __syncwarp();
+    if (done) break;
+  }
+  if (lane == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < p; ++i) tr += a[i + p * i].x;
+    for (int J = 0; J < p2; ++J) A_fin[J] = a[J];
+    info[0] = an_prev;
+    info[1] = tr;
+    info[2] = eta;
+    info[3] = (double)it;
+    info[4] = Rn2;
+  }
+}
+
+// B^[j][l] = coef sum_m sum_i X_m[i][j] Y_m[i][l], Y_m[i][l] = sum_k conj(A[i][k])
+// conj(X_m[k][l]) (A = the a that produced the last b, vec column-major),
+// coef = 1 / (n |a|^2 sc) with sc = p / tr A^ (tr A^ = p normalisation), read
+// from info; q x q row-major complex64 output.  Block = 32 x 32 tile of
+// (j, l), 256 threads, 4 outputs each; dynamic shared memory 2 n p 32 x 8 B.
+constexpr int kLrkTile = 32;
+__global__ void __launch_bounds__(256)
+k_lrk_bout(const float2* __restrict__ X, const double2* __restrict__ Aprev,
+           const double* __restrict__ info, int n, int p, int q, float2* __restrict__ Bout) {
+  constexpr int TB = kLrkTile;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float2 Ac[kLrkMaxP * kLrkMaxP];   // conj(A), row-major
+  const int np = n * p;
+  float2 (*Xj)[TB] = reinterpret_cast<float2 (*)[TB]>(smem);
+  float2 (*Yl)[TB] = reinterpret_cast<float2 (*)[TB]>(smem + (size_t)np * TB * sizeof(float2));
+  const float coef = (float)(info[1] / ((double)n * info[0] * (double)p));
+  const int j0 = blockIdx.y * TB, l0 = blockIdx.x * TB;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, k = e % p;
+    const double2 v = Aprev[i + p * k];
+    Ac[e] = make_float2((float)v.x, (float)-v.y);
+  }
+  for (int e = threadIdx.x; e < np * TB; e += blockDim.x) {
+    const int r = e / TB, c = e % TB;
+    Xj[r][c] = (j0 + c < q) ? X[(size_t)r * q + j0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * TB; e += blockDim.x) {
+    const int r = e / TB, c = e % TB, m = r / p, i = r % p;
+    float2 acc = make_float2(0.f, 0.f);
+    if (l0 + c < q)
+      for (int k = 0; k < p; ++k) {
+        const float2 x = X[(size_t)(m * p + k) * q + l0 + c];
+        acc = cadd(acc, cmul(Ac[i * p + k], cconj(x)));
+      }
+    Yl[r][c] = acc;
+  }
+  __syncthreads();
+  const int c = threadIdx.x % TB;
+  for (int rr = threadIdx.x / TB; rr < TB; rr += blockDim.x / TB) {
+    const int j = j0 + rr, l = l0 + c;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < np; ++r) acc = cadd(acc, cmul(Xj[r][rr], Yl[r][c]));
+    if (j < q && l < q) Bout[(size_t)j * q + l] = cscale(acc, coef);
+  }
+}
+
+}  // namespace kstap
