@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    ap.add_argument("--no-robustness", action="store_true",
+                    help="skip the SIRV / corrupted-training detection study")
     ap.add_argument("--no-paper-timing", action="store_true",
                     help="skip the single large-covariance LR-Kron timing grid")
     ap.add_argument("--no-precision-leg", action="store_true",
@@ -356,6 +358,45 @@ def precision_leg(dev, steps: int, warmup: int):
     return out
 
 
+# --------------------------------------------------- robustness (Sec. 5) ---
+def robustness_leg(dev):
+    """Detection on synthetic data under the SIRV texture and corrupted
+    training (Sec. 2, Sec. 5): a 512 x 512-cell cut of the 1024^2 frame model
+    with 400 targets (SNR U(0, 15) dB per element), clean / K-distributed
+    texture (nu = 0.5) / two copies of every target in its training ring /
+    both, with the Kron-STAP and the classical projector.  Pd = targets with
+    Tmax > tau at their cell; Pfa and mean Tmax over cells whose window holds
+    no target sample, planted copies included (sigma^2 = 1 is perfect
+    cancellation)."""
+    import dataclasses
+    import torch
+    import gen
+    from paper_1604_03622_b300.runner import KStap
+    wl = dataclasses.replace(gen.WORKLOADS["frame1024"].with_size(512, 512), n_targets=400)
+    out = dict(workload=f"{wl.name}, 400 targets", tau=wl.tau, rows=[])
+    for name, kw in (("clean", {}), ("sirv_nu0.5", dict(texture_nu=0.5)),
+                     ("training_targets_2", dict(training_targets=2)),
+                     ("both", dict(texture_nu=0.5, training_targets=2))):
+        f = gen.make_frame(wl, **kw)
+        busy = np.zeros((wl.H, wl.W), bool)      # cells whose window holds a target sample
+        for (r0, c0, v, beta) in f.targets + f.ring_targets:
+            if 0 <= r0 < wl.H:
+                busy[r0, max(0, c0 - wl.q + 1):max(0, c0 + wl.q)] = True
+        Y = torch.from_numpy(f.Y).to(dev)
+        for filt in ("kron", "classical"):
+            ks = KStap.from_workload(wl, f.bank_a, f.bank_b, device=str(dev), filter=filt)
+            o = ks.run(Y)
+            Tmax = o["Tmax"].cpu().numpy().reshape(wl.H, wl.W)
+            ks.close()
+            det = [Tmax[r0, c0] > wl.tau for (r0, c0, v, b) in f.targets]
+            free = Tmax[~busy]
+            out["rows"].append(dict(scenario=name, filter=filt, pd=float(np.mean(det)),
+                                    pfa=float(np.mean(free > wl.tau)),
+                                    mean_T_free=float(np.mean(free))))
+        del Y
+    return out
+
+
 # ------------------------------------------- paper's LR-Kron timing workload ---
 def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
     """One large-covariance LR-Kron fit (Sec. 7.1: rank-one A, B = I, n = 5) for
@@ -603,6 +644,8 @@ def main():
 
     precision = None if args.no_precision_leg else precision_leg(dev, 3, 3)
 
+    robustness = None if args.no_robustness else robustness_leg(dev)
+
     paper_timing = None if args.no_paper_timing else paper_timing_leg(
         dev, cpu=not args.no_cpu_baseline)
 
@@ -635,7 +678,8 @@ def main():
                                           ms_per_step=e2e_total / args.steps),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
-        batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing)
+        batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing,
+        robustness=robustness)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

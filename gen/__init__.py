@@ -32,7 +32,17 @@ Data model (Sec. 2 of the paper, SIRV clutter model, texture tau = 1):
     b_v[j] = exp(j 2 pi nu_v j).
 
 Random streams: numpy default_rng([seed, stream]), stream 0 = clutter,
-1 = noise, 2 = targets, 3 = sizes / arrivals / samples.
+1 = noise, 2 = targets, 3 = sizes / arrivals / samples, 4 = SIRV texture,
+5 = targets inside training rings.
+
+Robustness options of make_frame (Sec. 2 SIRV model, Sec. 5 robustness):
+  * texture_nu: each input range row's clutter is scaled by tau_row with
+    tau_row^2 ~ Gamma(nu, 1/nu) (mean 1): K-distributed clutter amplitude,
+    heavier-tailed for small nu; snapshots of one row share their texture,
+    as the SIRV model's per-snapshot tau does.
+  * training_targets: every target gets this many copies (same velocity and
+    amplitude) at random cells of its own training ring, which contaminates
+    its training set.
 """
 from __future__ import annotations
 
@@ -48,6 +58,8 @@ STREAM_CLUTTER = 0
 STREAM_NOISE = 1
 STREAM_TARGETS = 2
 STREAM_SIZES = 3
+STREAM_TEXTURE = 4
+STREAM_CONTAM = 5
 
 
 @dataclasses.dataclass
@@ -164,6 +176,7 @@ class Frame:
     A: np.ndarray                 # true spatial covariance (p x p)
     tones: np.ndarray             # clutter tones nu_k (cycles/sample)
     mus: np.ndarray               # clutter powers mu_k
+    ring_targets: List[Tuple[int, int, int, complex]] = dataclasses.field(default_factory=list)
 
 
 def _cn(rng: np.random.Generator, shape, dtype=np.float64) -> np.ndarray:
@@ -173,7 +186,8 @@ def _cn(rng: np.random.Generator, shape, dtype=np.float64) -> np.ndarray:
 
 
 def make_frame(wl: Workload, seed: Optional[int] = None, clutter: bool = True,
-               noise: bool = True, targets: bool = True) -> Frame:
+               noise: bool = True, targets: bool = True, texture_nu: Optional[float] = None,
+               training_targets: int = 0) -> Frame:
     """Draw one seeded frame for workload `wl` (see the module docstring)."""
     seed = wl.seed if seed is None else seed
     p, q, H_in, W_in = wl.p, wl.q, wl.H_in, wl.W_in
@@ -189,6 +203,10 @@ def make_frame(wl: Workload, seed: Optional[int] = None, clutter: bool = True,
     g = _cn(rng_c, (wl.r_b, H_in, p))                              # g_k(row)
     if clutter:
         lg = np.einsum("ij,krj->kri", L_A, g) * np.sqrt(mus)[:, None, None]
+        if texture_nu is not None:
+            rng_x = np.random.default_rng([seed, STREAM_TEXTURE])
+            tau = np.sqrt(rng_x.gamma(texture_nu, 1.0 / texture_nu, size=H_in))
+            lg = lg * tau[None, :, None]
         ph = np.exp(2j * np.pi * tones[:, None] * np.arange(W_in)[None, :])   # (r_b, W_in)
         for i in range(p):
             Y[i] += (lg[:, :, i].T @ ph).astype(np.complex64)     # (H_in, W_in)
@@ -214,8 +232,26 @@ def make_frame(wl: Workload, seed: Optional[int] = None, clutter: bool = True,
             blk = beta * np.outer(bank_a[v].astype(np.complex128), bank_b[v].astype(np.complex128))
             Y[:, r0 + wl.ring_r, c0 + wl.ring_a:c0 + wl.ring_a + q] += blk.astype(np.complex64)
             tl.append((r0, c0, v, complex(beta)))
+    ring: List[Tuple[int, int, int, complex]] = []
+    if training_targets > 0 and tl:
+        rng_k = np.random.default_rng([seed, STREAM_CONTAM])
+        for (r0, c0, v, beta) in list(tl):
+            blk = beta * np.outer(bank_a[v].astype(np.complex128), bank_b[v].astype(np.complex128))
+            placed = 0
+            while placed < training_targets:
+                dr = int(rng_k.integers(-wl.ring_r, wl.ring_r + 1))
+                dc = int(rng_k.integers(-wl.ring_a, wl.ring_a + 1))
+                if abs(dr) <= wl.guard_r and abs(dc) <= wl.guard_a:
+                    continue                        # in the guard box: not training
+                r1, c1 = r0 + dr, c0 + dc
+                if not (0 <= r1 + wl.ring_r < H_in and 0 <= c1 + wl.ring_a and
+                        c1 + wl.ring_a + q <= W_in):
+                    continue
+                Y[:, r1 + wl.ring_r, c1 + wl.ring_a:c1 + wl.ring_a + q] += blk.astype(np.complex64)
+                ring.append((r1, c1, v, beta))
+                placed += 1
     return Frame(wl=wl, Y=np.ascontiguousarray(Y), bank_a=bank_a, bank_b=bank_b, targets=tl,
-                 A=A, tones=tones, mus=mus)
+                 A=A, tones=tones, mus=mus, ring_targets=ring)
 
 
 def random_cells(wl: Workload, count: int, seed: int) -> np.ndarray:

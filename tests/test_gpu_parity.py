@@ -123,3 +123,16 @@ def test_parity_classical_filter(name, H, W):
     gpu = run_gpu(f, filter="classical")
     rep = compare(gpu, ref, np.arange(wl.H * wl.W), wl.tau, tol=5e-4)
     print("classical", name, H, W, rep)
+
+
+def test_parity_sirv_texture_and_ring_targets():
+    """K-distributed texture (nu = 0.5) and targets inside training rings change
+    only the input: the GPU still matches the oracle to the FP32 bar."""
+    import dataclasses
+    wl = dataclasses.replace(_wl("frame1024", 25, 60), n_targets=6)
+    f = gen.make_frame(wl, texture_nu=0.5, training_targets=2)
+    assert len(f.ring_targets) == 12
+    ref = oracle.run_workload(f)
+    gpu = run_gpu(f)
+    rep = compare(gpu, ref, np.arange(wl.H * wl.W), wl.tau)
+    print("sirv + ring targets", rep)
