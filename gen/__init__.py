@@ -320,3 +320,70 @@ def lrkron_timing_case(p: int, q: int, n: int = 5, sigma2: float = 0.1,
         rng_n = np.random.default_rng([seed, STREAM_NOISE])
         X = X + np.sqrt(sigma2) * _cn(rng_n, (n, p, q))
     return np.ascontiguousarray(X.astype(np.complex64))
+
+
+@dataclasses.dataclass
+class MultipassFrame:
+    wl: Workload                  # per-pass model (p channels); the frame has K p channels
+    K: int
+    Y: np.ndarray                 # (K p, H_in, W_in) complex64: pass k on channels [k p, (k+1) p)
+    bank_a: np.ndarray            # (K V, K p): velocity v of pass k = row k V + v, a_v on block k
+    bank_b: np.ndarray            # (K V, q)
+    targets: List[Tuple[int, int, int, int, complex]]   # (pass, r, c, v, beta)
+
+
+def make_multipass_frame(wl: Workload, K: int = 2, coherence: float = 0.9,
+                         seed: Optional[int] = None) -> MultipassFrame:
+    """K registered passes over the same scene (Sec. 3), stacked as K p channels.
+
+    The clutter of pass k is A_k^{1/2} g_k(row) exp(j 2 pi nu col) per tone,
+    with its own spatial covariance A_k (a per-pass phase phi_k: calibration
+    differs between passes) and temporal tones shared by all passes (same
+    ground); the range-row amplitudes g_k are correlated across passes with
+    coefficient `coherence` (g_k = c g_0 + sqrt(1 - c^2) e_k).  The stacked
+    clutter spans [U_A1; ...; U_AK] (x) U_B: spatial rank K, temporal rank r_b.
+    Noise is white per channel.  Each target moves between passes, so it is
+    injected in one pass only (pass chosen at random).  The bank holds every
+    velocity once per pass: row k V + v has a_v on the channels of pass k."""
+    seed = wl.seed + 17 if seed is None else seed
+    p, q, H_in, W_in = wl.p, wl.q, wl.H_in, wl.W_in
+    Y = np.zeros((K * p, H_in, W_in), dtype=np.complex64)
+    rng_c = np.random.default_rng([seed, STREAM_CLUTTER])
+    tones, band = clutter_tones(q, wl.r_b, rng_c)
+    w = 2.0 ** -np.arange(wl.r_b)
+    mus = wl.sigma2 * 10 ** (wl.cnr_db / 10.0) * w / w.sum()
+    g0 = _cn(rng_c, (wl.r_b, H_in))
+    ph = np.exp(2j * np.pi * tones[:, None] * np.arange(W_in)[None, :])   # (r_b, W_in)
+    for k in range(K):
+        phi = rng_c.uniform(-np.pi, np.pi)
+        L_A = np.linalg.cholesky(spatial_cov(p, phi))
+        gk = coherence * g0 + np.sqrt(1 - coherence ** 2) * _cn(rng_c, (wl.r_b, H_in))
+        h = _cn(rng_c, (wl.r_b, H_in, p))                 # spatial draw per tone and row
+        lg = np.einsum("ij,krj->kri", L_A, h) * (np.sqrt(mus)[:, None] * np.abs(gk))[:, :, None]
+        lg = lg * np.exp(1j * np.angle(gk))[:, :, None]
+        for i in range(p):
+            Y[k * p + i] += (lg[:, :, i].T @ ph).astype(np.complex64)
+    rng_n = np.random.default_rng([seed, STREAM_NOISE])
+    for ch in range(K * p):
+        Y[ch] += (np.sqrt(wl.sigma2) * _cn(rng_n, (H_in, W_in), np.float32)).astype(np.complex64)
+    ba, bb = steering_bank(p, q, wl.V)
+    bank_a = np.zeros((K * wl.V, K * p), np.complex64)
+    bank_b = np.zeros((K * wl.V, q), np.complex64)
+    for k in range(K):
+        bank_a[k * wl.V:(k + 1) * wl.V, k * p:(k + 1) * p] = ba
+        bank_b[k * wl.V:(k + 1) * wl.V] = bb
+    rng_t = np.random.default_rng([seed, STREAM_TARGETS])
+    nu = (np.arange(wl.V) - wl.V / 2.0) / wl.V
+    allowed = np.nonzero(np.abs(nu) >= max(0.15, band + 1.0 / q))[0]
+    tl = []
+    for _ in range(wl.n_targets):
+        kk = int(rng_t.integers(0, K))
+        r0, c0 = int(rng_t.integers(0, wl.H)), int(rng_t.integers(0, wl.W))
+        v = int(allowed[rng_t.integers(0, len(allowed))])
+        amp = np.sqrt(wl.sigma2 * 10 ** (rng_t.uniform(*wl.snr_db) / 10.0))
+        beta = amp * np.exp(1j * rng_t.uniform(-np.pi, np.pi))
+        blk = beta * np.outer(ba[v].astype(np.complex128), bb[v].astype(np.complex128))
+        Y[kk * p:(kk + 1) * p, r0 + wl.ring_r, c0 + wl.ring_a:c0 + wl.ring_a + q] += blk.astype(np.complex64)
+        tl.append((kk, r0, c0, v, complex(beta)))
+    return MultipassFrame(wl=wl, K=K, Y=np.ascontiguousarray(Y), bank_a=bank_a, bank_b=bank_b,
+                          targets=tl)

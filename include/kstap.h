@@ -62,10 +62,14 @@ typedef enum {
 /* Model and detector parameters.  Notation of the paper: p channels, q
  * pulses (azimuth window), ranks r_a, r_b of A and B (Eq. SparseOpt), Alg. 2
  * tolerance eps and iteration cap, detection threshold tau on Tmax.
- * Limits of this build: p == 3, q in {8, 16, 32}, r_a == 1 (the paper's
- * rank-one spatial model, Eq. KronCov), 1 <= r_b <= 4 with r_b < q (Sec. 5
- * warns against r_b close to q), ring >= guard >= 0, n >= 1,
- * (2 ring_r + 1)(2 ring_a + 1) <= 1024.  Other values give KSTAP_EINVAL. */
+ * Limits of this build: p == 3 with q in {8, 16, 32} and r_a == 1 (the
+ * paper's rank-one spatial model, Eq. KronCov); or p == 6 -- K = 2 registered
+ * passes of 3 channels stacked as one frame (Sec. 3), spatial rank r_a in
+ * {1, 2} -- with q in {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
+ * 1 <= r_b <= 4 with r_b < q (Sec. 5 warns against r_b close to q),
+ * ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1) <= 1024, and a
+ * training box whose tiles fit shared memory.  Other values give
+ * KSTAP_EINVAL. */
 typedef struct {
   int p, q, r_a, r_b;
   int ring_r, ring_a, guard_r, guard_a;
@@ -176,7 +180,8 @@ enum {
   KSTAP_K_FLIPFLOP = 2, /* Alg. 2 iterations on M, EIG_{r_a} (one thread per cell) */
   KSTAP_K_BFIT = 3,     /* exact lag sums -> B (float-float) -> EIG_{r_b} -> U_B */
   KSTAP_K_DETECT = 4,   /* Eq. KronSTAP projection and the velocity bank */
-  kstap_nkernels = 5
+  KSTAP_K_MGRAM = 5,    /* p = 6 (stacked passes): M = R R^H and A_0 from the lag store */
+  kstap_nkernels = 6
 };
 
 /* Per-kernel timing for measurement.  When enabled, every launch is
@@ -306,6 +311,18 @@ kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket);
  * last call's contents; the call clears what it needs zeroed itself. */
 kstap_status kstap_fit_project_noalloc(const kstap_params* params, const kstap_c64* Y, int H_in,
                                        int W_in, const kstap_factors* factors, void* cuda_stream);
+
+/* Noncoherent change detection over stacked passes (Sec. 8): from T_all of a
+ * kstap_detect whose bank lists every velocity once per pass (K V entries
+ * per cell, pass-major: entry k V + v = velocity v steered on pass k's
+ * channels), writes per cell Tmax_k = max_v T_all[cell][k V + v] (device,
+ * K x ncell, pass-major; may be NULL) and change = Tmax_{K-1} - Tmax_0
+ * (device, ncell; may be NULL): the difference of the filtered pixel
+ * magnitudes of the last and the first pass.  Asynchronous on cuda_stream.
+ * ncell = 0 is a no-op; ncell < 0, V < 1, K < 1 or a NULL T_all with
+ * ncell > 0 give KSTAP_EINVAL (message from kstap_last_error(NULL)). */
+kstap_status kstap_change_map(const float* T_all, long long ncell, int V, int K, float* Tmax_k,
+                              float* change, void* cuda_stream);
 
 /* One large-covariance LR-Kron fit (Alg. 2), the paper's timing workload
  * (Sec. 7.1): S = (1/n) sum_m x_m x_m^H from n snapshots x_m = vec(X_m^T),

@@ -24,8 +24,9 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_kernel_times", "kstap_fit_project_noalloc", "kstap_run_batch",
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
-            "kstap_release", "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit"]
-KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect"]
+            "kstap_release", "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
+            "kstap_change_map"]
+KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect", "mgram"]
 
 
 class KstapParams(ctypes.Structure):
@@ -107,6 +108,7 @@ def lib() -> ctypes.CDLL:
         L.kstap_lrkron_fit.argtypes = [P, I, I, I, I, ctypes.c_double, I, P, P,
                                        ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_double), P]
+        L.kstap_change_map.argtypes = [P, ctypes.c_longlong, I, I, P, P, P]
         L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]
         L.kstap_set_profiling.argtypes = [P, I]
@@ -116,7 +118,8 @@ def lib() -> ctypes.CDLL:
                      "kstap_run_batch", "kstap_graph_create", "kstap_graph_launch",
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
                      "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
-                     "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit"):
+                     "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
+                     "kstap_change_map"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -185,6 +188,23 @@ def kstap_lrkron_fit(X, r_a: int = 1, eps: float = 1e-6, max_iter: int = 100, A_
     _check(lib().kstap_lrkron_fit(_ptr(X), n, p, q, r_a, float(eps), int(max_iter), _ptr(A_out),
                                   _ptr(B_out), ctypes.byref(it), ctypes.byref(et), stream or None))
     return A_out, B_out, int(it.value), float(et.value)
+
+
+def kstap_change_map(T_all, V: int, K: int, Tmax_k=None, change=None, stream: int = 0):
+    """Per-pass maxima and the change map (Sec. 8) from T_all (ncell, K V)
+    float32 on the device.  Tmax_k (K, ncell) and change (ncell,) are float32
+    device tensors (allocated with torch when None).  Returns (Tmax_k, change)."""
+    import torch
+    ncell = T_all.shape[0]
+    if T_all.shape[1] != K * V or not T_all.is_contiguous():
+        raise ValueError("T_all must be a contiguous (ncell, K * V) tensor")
+    if Tmax_k is None:
+        Tmax_k = torch.empty(K, ncell, dtype=torch.float32, device=T_all.device)
+    if change is None:
+        change = torch.empty(ncell, dtype=torch.float32, device=T_all.device)
+    _check(lib().kstap_change_map(_ptr(T_all), ncell, V, K, _ptr(Tmax_k), _ptr(change),
+                                  stream or None))
+    return Tmax_k, change
 
 
 def kstap_device_status(ctx: int) -> None:

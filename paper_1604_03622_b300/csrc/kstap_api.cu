@@ -24,6 +24,7 @@
 #include "kstap_kernels.cuh"
 #include "kstap_tc.cuh"
 #include "kstap_lrk.cuh"
+#include "kstap_mp.cuh"
 
 using kstap::Geom;
 using kstap::Job;
@@ -142,16 +143,21 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "params is NULL";
     return false;
   }
-  if (p->p != 3) {
-    why = "this build supports p == 3";
+  if (p->p != 3 && p->p != 6) {
+    why = "this build supports p == 3, or p == 6 (two stacked passes)";
     return false;
   }
   if (p->q != 8 && p->q != 16 && p->q != 32) {
     why = "q must be 8, 16 or 32";
     return false;
   }
-  if (p->r_a != 1) {
-    why = "r_a must be 1 (rank-one spatial clutter model)";
+  if (p->p == 3 && p->r_a != 1) {
+    why = "r_a must be 1 for p == 3 (rank-one spatial clutter model)";
+    return false;
+  }
+  if (p->p == 6 && (p->q > 16 || p->r_a < 1 || p->r_a > 2 || p->precision != KSTAP_FP32 ||
+                    p->filter != KSTAP_FILTER_KRON)) {
+    why = "p == 6 (stacked passes) needs q in {8, 16}, r_a in {1, 2}, KSTAP_FP32 and the Kron filter";
     return false;
   }
   if (p->r_b < 1 || p->r_b > kstap::kRbMax || p->r_b >= p->q) {
@@ -256,7 +262,13 @@ int tiles_moments(int H, int W) {
   return ((W + kstap::kTileCells - 1) / kstap::kTileCells) *
          ((H + kstap::kMomRows - 1) / kstap::kMomRows);
 }
-int tiles_flip(int H, int W) { return (int)(((size_t)H * W + 127) / 128); }
+int tiles_flip(int H, int W, int p = 3) {
+  const size_t per = p <= 3 ? 128 : kstap::kWarpCells;   // thread per cell, or warp per cell
+  return (int)(((size_t)H * W + per - 1) / per);
+}
+int tiles_mgram(int H, int W, int p) {
+  return p <= 3 ? 0 : ((W + kstap::kWarpCells - 1) / kstap::kWarpCells) * H;
+}
 int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
 int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
 int tiles_detect(int H, int W, int q, int precision = KSTAP_FP32) {
@@ -315,7 +327,7 @@ std::vector<Frame> split_rows(const kstap_params& p, int V, const Frame& f, int 
 void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& fr, char* scratch,
                const Layout* L, std::vector<Job>& jobs, JobList& JL) {
   jobs.clear();
-  int t[4] = {0, 0, 0, 0};
+  int t[kstap::kKinds] = {0, 0, 0, 0, 0};
   for (size_t k = 0; k < fr.size(); ++k) {
     Job j;
     memset(&j, 0, sizeof(j));
@@ -343,8 +355,10 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
     j.tile0[kstap::kKindFlip] = t[1];
     j.tile0[kstap::kKindBfit] = t[2];
     j.tile0[kstap::kKindDetect] = t[3];
+    j.tile0[kstap::kKindMgram] = t[4];
     t[0] += tiles_moments(j.H, j.W);
-    t[1] += tiles_flip(j.H, j.W);
+    t[1] += tiles_flip(j.H, j.W, p.p);
+    t[4] += tiles_mgram(j.H, j.W, p.p);
     t[2] += tiles_bfit(j.H, j.W, g.tc);
     t[3] += tiles_detect(j.H, j.W, p.q, p.precision);
     jobs.push_back(j);
@@ -353,7 +367,7 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
   if (!jobs.empty()) JL.one = jobs[0];
   JL.table = nullptr;
   JL.njobs = (int)jobs.size();
-  for (int k = 0; k < 4; ++k) JL.ntiles[k] = t[k];
+  for (int k = 0; k < kstap::kKinds; ++k) JL.ntiles[k] = t[k];
   JL.NC = L ? (long long)L->NC : 0;
 }
 
@@ -363,8 +377,19 @@ size_t smem_moments(const Geom& g) {
   size_t b = (size_t)P * NRT * WT * 8;
   b += (b & 15);
   b += 2 * (size_t)PP * WT * 16;
-  b += (size_t)TR * PP * NUmax * 8;
+  if (P <= 3) b += (size_t)TR * PP * NUmax * 8;   // row lags for the per-thread M
   return b;
+}
+
+size_t smem_mgram(const Geom& g) {
+  const size_t PP = (size_t)g.p * g.p, NE = PP * (PP + 1) / 2;
+  const size_t NUmax = kstap::kWarpCells + g.q - 1;
+  return (NUmax * PP + kstap::kWarpCells * (NE + PP)) * 8;
+}
+
+size_t smem_flipw(const Geom& g) {
+  const size_t PP = (size_t)g.p * g.p, NE = PP * (PP + 1) / 2;
+  return kstap::kWarpCells * (NE + 3 * PP) * 8;
 }
 
 size_t smem_bfit(const Geom& g, bool from_store) {
@@ -387,6 +412,30 @@ size_t smem_detect(const Geom& g) {
   const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 4 * (size_t)P * R;
   const size_t cells = cells_per_detect_block(Q);
   return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8;
+}
+
+// Largest dynamic shared memory a CTA may opt into on sm_103a (227 KB).
+constexpr size_t kSmemOptin = 232448;
+
+// Checks every pass's shared-memory footprint for this geometry against the
+// per-CTA limit (the ring box and p set them).
+bool smem_fits(const Geom& g, bool lag_store, std::string& why) {
+  struct { const char* name; size_t bytes; } use[] = {
+      {"moments", smem_moments(g)},
+      {"B fit", smem_bfit(g, lag_store)},
+      {"detect", smem_detect(g)},
+      {"M gram", g.p > 3 ? smem_mgram(g) : 0},
+      {"warp flip-flop", g.p > 3 ? smem_flipw(g) : 0},
+  };
+  for (const auto& u : use)
+    if (u.bytes > kSmemOptin) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "the %s pass needs %zu B of shared memory per CTA (limit %zu B); "
+               "use a smaller training ring", u.name, u.bytes, kSmemOptin);
+      why = buf;
+      return false;
+    }
+  return true;
 }
 
 // Persistent grid: SMs x resident CTAs x waves, capped by the tile count.
@@ -440,16 +489,45 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
   prof_end(prof, KSTAP_K_MOMENTS, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
 
-  const int g2 = grid_for(kstap::k_flipflop<P>, 128, 0, JL.ntiles[kstap::kKindFlip], sm_count,
-                          waves);
-  prof_collect(prof, KSTAP_K_FLIPFLOP);
-  prof_begin(prof, KSTAP_K_FLIPFLOP, s);
-  kstap::k_flipflop<P><<<g2, 128, 0, s>>>(g, JL, Mw, Sw, aw);
-  prof_end(prof, KSTAP_K_FLIPFLOP, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
+  if constexpr (P <= 3) {
+    const int g2 = grid_for(kstap::k_flipflop<P>, 128, 0, JL.ntiles[kstap::kKindFlip], sm_count,
+                            waves);
+    prof_collect(prof, KSTAP_K_FLIPFLOP);
+    prof_begin(prof, KSTAP_K_FLIPFLOP, s);
+    kstap::k_flipflop<P><<<g2, 128, 0, s>>>(g, JL, Mw, Sw, aw);
+    prof_end(prof, KSTAP_K_FLIPFLOP, s);
+    KSTAP_CUDA(ctx, cudaGetLastError());
+  } else {
+    // stacked passes: M and the block sums from the lag store (a warp per
+    // cell), then Alg. 2 with a warp per cell
+    if (!lag_store) return fail(ctx, KSTAP_EINVAL, "p > 3 needs the lag store");
+    const size_t smg = smem_mgram(g);
+    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_mgram<P, Q>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
+    const int gm = grid_for(kstap::k_mgram<P, Q>, kstap::kWarpCells * 32, smg,
+                            JL.ntiles[kstap::kKindMgram], sm_count, waves);
+    prof_collect(prof, KSTAP_K_MGRAM);
+    prof_begin(prof, KSTAP_K_MGRAM, s);
+    kstap::k_mgram<P, Q><<<gm, kstap::kWarpCells * 32, smg, s>>>(g, JL, Mw, Sw, Lw);
+    prof_end(prof, KSTAP_K_MGRAM, s);
+    KSTAP_CUDA(ctx, cudaGetLastError());
+    const size_t smf = smem_flipw(g);
+    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_flipflop_w<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
+    const int gf = grid_for(kstap::k_flipflop_w<P>, kstap::kWarpCells * 32, smf,
+                            JL.ntiles[kstap::kKindFlip], sm_count, waves);
+    prof_collect(prof, KSTAP_K_FLIPFLOP);
+    prof_begin(prof, KSTAP_K_FLIPFLOP, s);
+    kstap::k_flipflop_w<P><<<gf, kstap::kWarpCells * 32, smf, s>>>(g, JL, Mw, Sw, aw);
+    prof_end(prof, KSTAP_K_FLIPFLOP, s);
+    KSTAP_CUDA(ctx, cudaGetLastError());
+  }
 
   const size_t sm3 = smem_bfit(g, lag_store);
-  auto kb = lag_store ? kstap::k_bfit<P, Q, R, true> : kstap::k_bfit<P, Q, R, false>;
+  auto kb = kstap::k_bfit<P, Q, R, true>;
+  if constexpr (P <= 3) {
+    if (!lag_store) kb = kstap::k_bfit<P, Q, R, false>;
+  }
   KSTAP_CUDA(ctx, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   constexpr int nt3 = kstap::bfit_threads(Q);
   const int g3 = grid_for(kb, nt3, sm3, JL.ntiles[kstap::kKindBfit], sm_count, waves);
@@ -478,23 +556,37 @@ kstap_status enqueue_detect_tc(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, c
   return KSTAP_OK;
 }
 
+template <int P, int Q, int R, int RA>
+kstap_status enqueue_detect_fp32(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                                 int sm_count, int waves, cudaStream_t s);
+
 template <int P, int Q, int R>
 kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                             int sm_count, int waves, cudaStream_t s) {
   if (JL.njobs < 1) return KSTAP_OK;
-  if (ctx->prm.precision == KSTAP_FP16X3)
-    return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
-  if (ctx->prm.precision == KSTAP_BF16X3)
-    return enqueue_detect_tc<P, Q, R, true>(ctx, prof, g, JL, sm_count, waves, s);
+  if constexpr (P <= 3) {
+    if (ctx->prm.precision == KSTAP_FP16X3)
+      return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
+    if (ctx->prm.precision == KSTAP_BF16X3)
+      return enqueue_detect_tc<P, Q, R, true>(ctx, prof, g, JL, sm_count, waves, s);
+  } else {
+    if (ctx->prm.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
+  }
+  return enqueue_detect_fp32<P, Q, R, 1>(ctx, prof, g, JL, sm_count, waves, s);
+}
+
+template <int P, int Q, int R, int RA>
+kstap_status enqueue_detect_fp32(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                                 int sm_count, int waves, cudaStream_t s) {
   const size_t sm = smem_detect(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R>,
+  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R, RA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const int grid = grid_for(kstap::k_detect<P, Q, R>, kstap::kThreads, sm,
+  const int grid = grid_for(kstap::k_detect<P, Q, R, RA>, kstap::kThreads, sm,
                             JL.ntiles[kstap::kKindDetect], sm_count, waves);
   prof_collect(prof, KSTAP_K_DETECT);
   prof_begin(prof, KSTAP_K_DETECT, s);
-  kstap::k_detect<P, Q, R><<<grid, kstap::kThreads, sm, s>>>(g, JL, ctx->bank_aT, ctx->bank_bT,
-                                                               ctx->bank_n2);
+  kstap::k_detect<P, Q, R, RA><<<grid, kstap::kThreads, sm, s>>>(g, JL, ctx->bank_aT,
+                                                                   ctx->bank_bT, ctx->bank_n2);
   prof_end(prof, KSTAP_K_DETECT, s);
   KSTAP_CUDA(ctx, cudaGetLastError());
   return KSTAP_OK;
@@ -510,9 +602,22 @@ kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, cons
   KSTAP_DISPATCH(32, 1, CALLT(32, 1)) KSTAP_DISPATCH(32, 2, CALLT(32, 2)) \
   KSTAP_DISPATCH(32, 3, CALLT(32, 3)) KSTAP_DISPATCH(32, 4, CALLT(32, 4))
 
+#define KSTAP_DISPATCH_P6(CALLT)                                          \
+  KSTAP_DISPATCH(8, 1, CALLT(8, 1)) KSTAP_DISPATCH(8, 2, CALLT(8, 2))     \
+  KSTAP_DISPATCH(8, 3, CALLT(8, 3)) KSTAP_DISPATCH(8, 4, CALLT(8, 4))     \
+  KSTAP_DISPATCH(16, 1, CALLT(16, 1)) KSTAP_DISPATCH(16, 2, CALLT(16, 2)) \
+  KSTAP_DISPATCH(16, 3, CALLT(16, 3)) KSTAP_DISPATCH(16, 4, CALLT(16, 4))
+
 kstap_status dispatch_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                           char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
                           cudaStream_t s) {
+  if (g.p == 6) {
+#define KSTAP_FIT6(QQ, RR) \
+  enqueue_fit<6, QQ, RR>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s)
+    KSTAP_DISPATCH_P6(KSTAP_FIT6)
+#undef KSTAP_FIT6
+    return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b) for p = 6");
+  }
 #define KSTAP_FITC(QQ, RR) \
   enqueue_fit<3, QQ, RR>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s)
   KSTAP_DISPATCH_ALL(KSTAP_FITC)
@@ -522,6 +627,12 @@ kstap_status dispatch_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const 
 
 kstap_status dispatch_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                              int sm_count, int waves, cudaStream_t s) {
+  if (g.p == 6) {
+#define KSTAP_DET6(QQ, RR) enqueue_detect<6, QQ, RR>(ctx, prof, g, JL, sm_count, waves, s)
+    KSTAP_DISPATCH_P6(KSTAP_DET6)
+#undef KSTAP_DET6
+    return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b) for p = 6");
+  }
 #define KSTAP_DETC(QQ, RR) enqueue_detect<3, QQ, RR>(ctx, prof, g, JL, sm_count, waves, s)
   KSTAP_DISPATCH_ALL(KSTAP_DETC)
 #undef KSTAP_DETC
@@ -626,6 +737,8 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
   if (!valid_params(params, why)) return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
   if (V < 1 || V > 256) return fail(nullptr, KSTAP_EINVAL, "V must be in [1, 256]");
   if (!bank_a || !bank_b) return fail(nullptr, KSTAP_EINVAL, "bank is NULL");
+  if (!smem_fits(make_geom(*params, V, 0), true, why))
+    return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
   kstap_ctx* ctx = new kstap_ctx();
   ctx->prm = *params;
   ctx->V = V;
@@ -1520,6 +1633,10 @@ extern "C" kstap_status kstap_fit_project_noalloc(const kstap_params* params, co
                                                   void* cuda_stream) {
   std::string why;
   if (!valid_params(params, why)) return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
+  if (params->p != 3)
+    return fail(nullptr, KSTAP_EINVAL, "kstap_fit_project_noalloc handles p == 3 only");
+  if (!smem_fits(make_geom(*params, 1, 0), false, why))
+    return fail(nullptr, KSTAP_EINVAL, "%s", why.c_str());
   if (!Y) return fail(nullptr, KSTAP_EINVAL, "Y is NULL");
   if (!factors || !factors->UA || !factors->UB_hi || !factors->UB_lo)
     return fail(nullptr, KSTAP_EINVAL, "factors (UA, UB_hi, UB_lo) must be non-NULL");
@@ -1606,4 +1723,18 @@ extern "C" kstap_status kstap_lrkron_fit(const kstap_c64* X, int n, int p, int q
   if (iters) *iters = (int32_t)hinfo[3];
   if (eta) *eta = hinfo[2];
   return res;
+}
+
+extern "C" kstap_status kstap_change_map(const float* T_all, long long ncell, int V, int K,
+                                         float* Tmax_k, float* change, void* cuda_stream) {
+  if (ncell < 0 || V < 1 || K < 1 || (ncell > 0 && !T_all))
+    return fail(nullptr, KSTAP_EINVAL, "kstap_change_map: need ncell >= 0, V >= 1, K >= 1, T_all");
+  if (ncell == 0) return KSTAP_OK;
+  const unsigned blocks = (unsigned)std::min<long long>((ncell + 255) / 256, 148LL * 16);
+  kstap::k_change<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(T_all, ncell, V, K, Tmax_k,
+                                                                 change);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(nullptr, KSTAP_ECUDA, "kstap_change_map: %s", cudaGetErrorString(e));
+  return KSTAP_OK;
 }

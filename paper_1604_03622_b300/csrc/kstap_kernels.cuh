@@ -59,7 +59,8 @@ struct Geom {
 // One frame of a batch.  Per-cell workspace arrays of a launch are
 // struct-of-arrays over all cells of all jobs (stride NC), this job's cells
 // starting at cell0; its lag store starts at lag0 (float4 units).
-enum { kKindMoments = 0, kKindFlip = 1, kKindBfit = 2, kKindDetect = 3 };
+enum { kKindMoments = 0, kKindFlip = 1, kKindBfit = 2, kKindDetect = 3, kKindMgram = 4,
+       kKinds = 5 };
 struct Job {
   const float2* Y;              // first row of this job's rows, channel 0
   int H_in, W_in, H, W;         // rows / columns of this job (a frame or a row strip of one)
@@ -77,7 +78,7 @@ struct Job {
   int32_t* vidx;
   uint8_t* map;
   float* T_all;
-  int tile0[4];                 // first tile of this job in each kernel's tile space
+  int tile0[kKinds];            // first tile of this job in each kernel's tile space
 };
 
 // A launch's jobs: one job passed by value (table == nullptr), or a device
@@ -86,7 +87,7 @@ struct JobList {
   Job one;
   const Job* table;
   int njobs;
-  int ntiles[4];
+  int ntiles[kKinds];
   long long NC;                 // total cells (stride of the per-cell workspace arrays)
   unsigned long long* report;   // optional counters: [0] cells at max_iter, [1] cells flagged non-finite
 };
@@ -341,7 +342,12 @@ __global__ void __launch_bounds__(kMomThreads)
 k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
           float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
-  constexpr int NE = PP * (PP + 1) / 2;
+  // the per-thread Gram M (and the block sums) only for P <= 3; for more
+  // channels (stacked passes) this pass writes the lag store and k_mgram forms
+  // M and the block sums from it with a warp per cell
+  constexpr bool kThreadM = P <= 3;
+  constexpr int NE = kThreadM ? PP * (PP + 1) / 2 : 1;
+  constexpr int NS = kThreadM ? PP : 1;
   constexpr int TC = kTileCells;
   constexpr int TR = kMomRows;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -386,11 +392,11 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
 
   const int tr = threadIdx.x / TC, cl = threadIdx.x % TC;
   const bool live = (c0 + cl) < g.W && (r0 + tr) < g.H;
-  float wr[NE], wi[NE], sr[PP], si[PP];
+  float wr[NE], wi[NE], sr[NS], si[NS];
 #pragma unroll
   for (int e = 0; e < NE; ++e) wr[e] = wi[e] = 0.f;
 #pragma unroll
-  for (int J = 0; J < PP; ++J) sr[J] = si[J] = 0.f;
+  for (int J = 0; J < NS; ++J) sr[J] = si[J] = 0.f;
 
   const int g0 = g.Rr - g.Gr, g1 = g.Rr + g.Gr;
   for (int lagg = Q - 1; lagg >= 0; --lagg) {
@@ -481,13 +487,14 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
           float4 v;
           ll_to_ff(L.x, v.x, v.y);
           ll_to_ff(L.y, v.z, v.w);
-          lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
+          if constexpr (kThreadM) lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
           if (Lw && (u < TC || last_tile) && c0 + u < WL && r0 + t < g.H)
             Lw[(((size_t)(r0 + t) * Q + lagg) * PP + J) * WL + c0 + u] = v;
         }
       }
       __syncthreads();
     }
+    if constexpr (kThreadM) {
     if (lagg == 0) {
       // fold the negative lags: W += conj(Pi W Pi^T), s += conj(Pi s)
 #pragma unroll
@@ -532,6 +539,8 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
         }
       }
     }
+    }
+    if constexpr (kThreadM) {
     if (live) {
       const float2* lt = lag + (size_t)tr * PP * NUmax;
       for (int j = 0; j < Q - lagg; ++j) {
@@ -551,8 +560,10 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
         }
       }
     }
+    }
     __syncthreads();
   }
+  if constexpr (kThreadM) {
   if (live) {
     const size_t ncell = (size_t)JL.NC;
     const size_t cell = (size_t)JB.cell0 + (size_t)(r0 + tr) * g.W + (c0 + cl);
@@ -560,6 +571,7 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     for (int e = 0; e < NE; ++e) Mw[e * ncell + cell] = make_float2(wr[e], wi[e]);
 #pragma unroll
     for (int J = 0; J < PP; ++J) Sw[J * ncell + cell] = make_float2(sr[J], si[J]);
+  }
   }
   __syncthreads();
   }  // tile loop
@@ -592,9 +604,18 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
 #pragma unroll
       for (int q = p + 1; q < N; ++q) {
         const float2 b = A[p][q];
-        const float ab = sqrtf(cabs2(b));
-        if (ab == 0.f) continue;
-        const float2 ph = make_float2(b.x / ab, b.y / ab);          // e^{i phi}
+        // |b| without squaring (|b|^2 of a small off-diagonal entry falls
+        // into the subnormal range and loses its digits); an entry below
+        // 1e-10 of the diagonal pair is dropped: a rotation that small
+        // changes nothing at single precision
+        const float ab = hypotf(b.x, b.y);
+        if (!(ab > 1e-10f * (fabsf(A[p][p].x) + fabsf(A[q][q].x)))) {
+          A[p][q] = A[q][p] = make_float2(0.f, 0.f);
+          continue;
+        }
+        float2 ph = make_float2(b.x / ab, b.y / ab);                // e^{i phi}
+        const float pn = rsqrtf(cabs2(ph));                          // |ph| = 1 to rounding
+        ph = make_float2(ph.x * pn, ph.y * pn);
         const float tau = (A[q][q].x - A[p][p].x) / (2.f * ab);
         const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
         const float c = rsqrtf(1.f + tt * tt);
@@ -1244,7 +1265,7 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
 // numerator with the projected steering factors keeps it well conditioned
 // when d_v lies close to the clutter subspace; with Z float-float accurate,
 // the error of T_v is ~2 eps sqrt(q) / sqrt(d^H P d / |d|^2).
-template <int P, int Q, int R>
+template <int P, int Q, int R, int RA = 1>
 __global__ void __launch_bounds__(kThreads)
 k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
          const float2* __restrict__ bank_bT, const float* __restrict__ bank_n2) {
@@ -1285,7 +1306,8 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float2* Zs = Xs + P * Q;             // [P][Q]
   float2* Uh = Zs + P * Q;             // [Q][R]
   float2* Ul = Uh + Q * R;             // [Q][R]
-  float2* Ua = Ul + Q * R;             // [P]   (r_a = 1)
+  static_assert(RA >= 1 && RA <= 2, "the scratch holds U_A for r_a <= 2");
+  float2* Ua = Ul + Q * R;             // [P][RA] (2P slots)
   float4* Cs = reinterpret_cast<float4*>(Ua + 2 * P);   // [P][R] float-float complex
   float4* Es = Cs + P * R;                               // [P][R] F_A C, float-float (classical)
   if (live) {
@@ -1299,7 +1321,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       Uh[gl * R + m] = UBh[(cell * Q + gl) * R + m];
       Ul[gl * R + m] = UBl[(cell * Q + gl) * R + m];
     }
-    if (gl < P) Ua[gl] = UA[cell * P + gl];
+    for (int e = gl; e < P * RA; e += G) Ua[e] = UA[cell * P * RA + e];   // [i][m]
   }
   __syncwarp();
   // C[i][m] = sum_j X[i][j] conj(U[j][m]), float-float
@@ -1378,13 +1400,22 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       }
       z[i] = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
     }
-    float2 t = make_float2(0.f, 0.f);
-    if (!classical) {
+    float2 t[RA];   // U_A^H z: F_A z = z - U_A t (none for the classical filter)
 #pragma unroll
-      for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], z[i]));
+    for (int m = 0; m < RA; ++m) {
+      t[m] = make_float2(0.f, 0.f);
+      if (!classical) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) t[m] = cadd(t[m], cmulc(Ua[i * RA + m], z[i]));
+      }
     }
 #pragma unroll
-    for (int i = 0; i < P; ++i) Zs[i * Q + j] = csub(z[i], cmul(Ua[i], t));
+    for (int i = 0; i < P; ++i) {
+      float2 zi = z[i];
+#pragma unroll
+      for (int m = 0; m < RA; ++m) zi = csub(zi, cmul(Ua[i * RA + m], t[m]));
+      Zs[i * Q + j] = zi;
+    }
   }
   __syncwarp();
   float best = -1.f;
@@ -1479,14 +1510,20 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       for (int k = 0; k < VB; ++k) {
         if (base + k * G + gl >= V) break;
         const int v = base + k * G + gl;
-        float2 t = make_float2(0.f, 0.f);
+        float2 t[RA];   // U_A^H a_v
 #pragma unroll
-        for (int i = 0; i < P; ++i) t = cadd(t, cmulc(Ua[i], aT[i * V + v]));
+        for (int m = 0; m < RA; ++m) {
+          t[m] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < P; ++i) t[m] = cadd(t[m], cmulc(Ua[i * RA + m], aT[i * V + v]));
+        }
         float dA = 0.f;
         float2 num = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-          const float2 wa = csub(aT[i * V + v], cmul(Ua[i], t));
+          float2 wa = aT[i * V + v];
+#pragma unroll
+          for (int m = 0; m < RA; ++m) wa = csub(wa, cmul(Ua[i * RA + m], t[m]));
           dA += cabs2(wa);
           num = cadd(num, cmulc(classical ? aT[i * V + v] : wa, y[k][i]));
         }

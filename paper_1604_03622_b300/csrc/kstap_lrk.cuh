@@ -108,9 +108,14 @@ __device__ void lrk_jacobi(double2* A, int p, double* w, double2* U) {
     for (int a = 0; a < p - 1; ++a)
       for (int b = a + 1; b < p; ++b) {
         const double2 apq = A[a * p + b];
-        const double ab = sqrt(zabs2(apq));
-        if (ab == 0.0) continue;
-        const double2 ph = make_double2(apq.x / ab, apq.y / ab);
+        const double ab = hypot(apq.x, apq.y);   // no squaring: no underflow for tiny entries
+        if (!(ab > 1e-20 * (fabs(A[a * p + a].x) + fabs(A[b * p + b].x)))) {
+          A[a * p + b] = A[b * p + a] = make_double2(0.0, 0.0);
+          continue;
+        }
+        double2 ph = make_double2(apq.x / ab, apq.y / ab);
+        const double pn = 1.0 / sqrt(zabs2(ph));
+        ph = make_double2(ph.x * pn, ph.y * pn);
         const double tau = (A[b * p + b].x - A[a * p + a].x) / (2.0 * ab);
         const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
         const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;

@@ -42,12 +42,31 @@ def test_create_rejects_unsupported_parameters_without_gpu():
         K.make_params(3, 16, 1, 3, 12, 24, 1, 1, 10.0),  # box > 1024
         K.make_params(3, 16, 1, 3, 4, 7, 1, 2, 10.0, filter="classical",
                       precision="fp16x3"),                # classical filter: FP32 route only
+        K.make_params(6, 32, 2, 3, 4, 7, 1, 2, 10.0),    # stacked passes: q <= 16
+        K.make_params(6, 16, 3, 3, 4, 7, 1, 2, 10.0),    # stacked passes: r_a <= 2
+        K.make_params(6, 16, 2, 3, 4, 7, 1, 2, 10.0, precision="fp16x3"),
+        K.make_params(6, 16, 2, 3, 4, 7, 1, 2, 10.0, filter="classical"),
     ]
     dummy = np.zeros(64, np.complex64)   # never dereferenced: validation fails first
     for prm in bad:
         with pytest.raises(K.KstapError, match="EINVAL"):
             K.kstap_create(prm, _Fake(dummy), _Fake(dummy), 8)
         assert K.kstap_last_error(None) != ""
+
+
+def test_noalloc_and_change_map_reject_without_gpu():
+    import ctypes
+    dummy = np.zeros(64, np.complex64)
+    fac = K.make_factors(_Fake(dummy), _Fake(dummy), _Fake(dummy))
+    prm = K.make_params(6, 8, 2, 2, 4, 7, 1, 2, 10.0)    # stacked passes: context path only
+    with pytest.raises(K.KstapError, match="EINVAL"):
+        K.kstap_fit_project_noalloc(prm, _Fake(dummy), 20, 40, fac)
+    t = np.zeros(8, np.float32)
+    for ncell, V, Kp in ((4, 0, 2), (4, 2, 0), (-1, 2, 2)):
+        st = K.lib().kstap_change_map(t.ctypes.data, ncell, V, Kp, None, None, None)
+        assert K.STATUS[st] == "KSTAP_EINVAL"
+    # no cells: nothing to do, nothing launched
+    assert K.lib().kstap_change_map(None, 0, 2, 2, None, None, None) == K.KSTAP_OK
 
 
 def test_workspace_size_formula():
