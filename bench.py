@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
     ap.add_argument("--no-robustness", action="store_true",
                     help="skip the SIRV / corrupted-training detection study")
+    ap.add_argument("--no-multipass", action="store_true",
+                    help="skip the two-pass (p = 6) stacked frame and change map")
     ap.add_argument("--no-paper-timing", action="store_true",
                     help="skip the single large-covariance LR-Kron timing grid")
     ap.add_argument("--no-precision-leg", action="store_true",
@@ -397,6 +399,60 @@ def robustness_leg(dev):
     return out
 
 
+# ------------------------------------------------ stacked passes (Sec. 8) ---
+def multipass_leg(dev, steps: int, warmup: int, H: int = 1024, W: int = 1024):
+    """Two registered passes of the 1024^2 frame model (q = 16, r_b = 3,
+    n = 120, V = 64 per pass, 40 dB CNR, pass-to-pass clutter coherence 0.9)
+    stacked as p = 6 channels with r_a = 2: fit + detect over the 2V-entry
+    bank per step (CUDA events, L2 flushed between steps), then the change
+    map.  Change Pd: targets (each present in one pass) whose cell has
+    |change| > tau with the sign of their pass; change Pfa: cells whose
+    window holds no target sample with |change| > tau."""
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    wl = gen.WORKLOADS["frame1024"].with_size(H, W)
+    f = gen.make_multipass_frame(wl, K=2)
+    Y = torch.from_numpy(f.Y).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ks = KStap(2 * wl.p, wl.q, 2, wl.r_b, wl.ring_r, wl.ring_a, wl.guard_r, wl.guard_a, wl.tau,
+               f.bank_a, f.bank_b, device=str(dev), stream=stream)
+    for _ in range(warmup):
+        ks.run(Y, T_all=True)
+    torch.cuda.synchronize(dev)
+    K.kstap_set_profiling(ks.ctx, True)
+    ms, cms = [], []
+    for s in range(steps):
+        flush.fill_(s & 0xff)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        o = ks.run(Y, T_all=True)
+        b.record(stream)
+        Tk, ch = K.kstap_change_map(o["T_all"], wl.V, 2, stream=stream.cuda_stream)
+        c.record(stream)
+        c.synchronize()
+        ms.append(a.elapsed_time(b))
+        cms.append(b.elapsed_time(c))
+    kt = K.kstap_kernel_times(ks.ctx)
+    ch = ch.cpu().numpy().reshape(wl.H, wl.W)
+    ks.close()
+    busy = np.zeros((wl.H, wl.W), bool)
+    for (kk, r0, c0, v, beta) in f.targets:
+        busy[r0, max(0, c0 - wl.q + 1):c0 + wl.q] = True
+    hits = [abs(ch[r0, c0]) > wl.tau and np.sign(ch[r0, c0]) == (1 if kk == 1 else -1)
+            for (kk, r0, c0, v, beta) in f.targets]
+    del Y, flush
+    torch.cuda.empty_cache()
+    return dict(workload=f"{wl.name} x 2 passes", cells_per_frame=wl.cells, p=6, q=wl.q, r_a=2,
+                r_b=wl.r_b, V_bank=2 * wl.V, cells_per_s=wl.cells * len(ms) / (sum(ms) / 1e3),
+                ms_per_frame=sum(ms) / len(ms), change_map_ms=sum(cms) / len(cms),
+                kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items() if v[1]},
+                change_pd=float(np.mean(hits)), change_pfa=float(np.mean(np.abs(ch[~busy]) > wl.tau)),
+                targets=len(f.targets), tau=wl.tau)
+
+
 # ------------------------------------------- paper's LR-Kron timing workload ---
 def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
     """One large-covariance LR-Kron fit (Sec. 7.1: rank-one A, B = I, n = 5) for
@@ -646,6 +702,8 @@ def main():
 
     robustness = None if args.no_robustness else robustness_leg(dev)
 
+    multipass = None if args.no_multipass else multipass_leg(dev, 3, 2)
+
     paper_timing = None if args.no_paper_timing else paper_timing_leg(
         dev, cpu=not args.no_cpu_baseline)
 
@@ -679,7 +737,7 @@ def main():
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
         batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing,
-        robustness=robustness)
+        robustness=robustness, multipass=multipass)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

@@ -263,7 +263,7 @@ int tiles_moments(int H, int W) {
          ((H + kstap::kMomRows - 1) / kstap::kMomRows);
 }
 int tiles_flip(int H, int W, int p = 3) {
-  const size_t per = p <= 3 ? 128 : kstap::kWarpCells;   // thread per cell, or warp per cell
+  const size_t per = p <= 3 ? 128 : kstap::kFlipThreads;   // a thread per cell
   return (int)(((size_t)H * W + per - 1) / per);
 }
 int tiles_mgram(int H, int W, int p) {
@@ -382,14 +382,14 @@ size_t smem_moments(const Geom& g) {
 }
 
 size_t smem_mgram(const Geom& g) {
-  const size_t PP = (size_t)g.p * g.p, NE = PP * (PP + 1) / 2;
+  const size_t PP = (size_t)g.p * g.p;
   const size_t NUmax = kstap::kWarpCells + g.q - 1;
-  return (NUmax * PP + kstap::kWarpCells * (NE + PP)) * 8;
+  return (NUmax * PP + kstap::kWarpCells * (PP * PP + PP)) * 8;
 }
 
-size_t smem_flipw(const Geom& g) {
-  const size_t PP = (size_t)g.p * g.p, NE = PP * (PP + 1) / 2;
-  return kstap::kWarpCells * (NE + 3 * PP) * 8;
+size_t smem_flipt(const Geom& g) {
+  // a, y = M a and the two leading eigenvectors of each thread
+  return (2 * (size_t)g.p * g.p + 2 * (size_t)g.p) * kstap::kFlipThreads * 8;
 }
 
 size_t smem_bfit(const Geom& g, bool from_store) {
@@ -425,7 +425,7 @@ bool smem_fits(const Geom& g, bool lag_store, std::string& why) {
       {"B fit", smem_bfit(g, lag_store)},
       {"detect", smem_detect(g)},
       {"M gram", g.p > 3 ? smem_mgram(g) : 0},
-      {"warp flip-flop", g.p > 3 ? smem_flipw(g) : 0},
+      {"flip-flop", g.p > 3 ? smem_flipt(g) : 0},
   };
   for (const auto& u : use)
     if (u.bytes > kSmemOptin) {
@@ -499,7 +499,7 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
     KSTAP_CUDA(ctx, cudaGetLastError());
   } else {
     // stacked passes: M and the block sums from the lag store (a warp per
-    // cell), then Alg. 2 with a warp per cell
+    // cell), then Alg. 2 with a thread per cell
     if (!lag_store) return fail(ctx, KSTAP_EINVAL, "p > 3 needs the lag store");
     const size_t smg = smem_mgram(g);
     KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_mgram<P, Q>,
@@ -511,14 +511,14 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
     kstap::k_mgram<P, Q><<<gm, kstap::kWarpCells * 32, smg, s>>>(g, JL, Mw, Sw, Lw);
     prof_end(prof, KSTAP_K_MGRAM, s);
     KSTAP_CUDA(ctx, cudaGetLastError());
-    const size_t smf = smem_flipw(g);
-    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_flipflop_w<P>,
+    const size_t smf = smem_flipt(g);
+    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_flipflop_t<P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
-    const int gf = grid_for(kstap::k_flipflop_w<P>, kstap::kWarpCells * 32, smf,
+    const int gf = grid_for(kstap::k_flipflop_t<P>, kstap::kFlipThreads, smf,
                             JL.ntiles[kstap::kKindFlip], sm_count, waves);
     prof_collect(prof, KSTAP_K_FLIPFLOP);
     prof_begin(prof, KSTAP_K_FLIPFLOP, s);
-    kstap::k_flipflop_w<P><<<gf, kstap::kWarpCells * 32, smf, s>>>(g, JL, Mw, Sw, aw);
+    kstap::k_flipflop_t<P><<<gf, kstap::kFlipThreads, smf, s>>>(g, JL, Mw, Sw, aw);
     prof_end(prof, KSTAP_K_FLIPFLOP, s);
     KSTAP_CUDA(ctx, cudaGetLastError());
   }

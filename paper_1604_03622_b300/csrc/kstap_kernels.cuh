@@ -582,10 +582,13 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
 // return d[] holds the eigenvalues and the columns of U the eigenvectors,
 // sorted by decreasing eigenvalue.
 // WANT_U = false skips the eigenvector accumulation (eigenvalues only);
-// sweeps stop once sum_{i<j} |A_ij|^2 <= tol * sum_i A_ii^2.
+// sweeps stop once sum_{i<j} |A_ij|^2 <= tol * sum_i A_ii^2.  Off-diagonal
+// entries at or below max(1e-10 (|A_pp| + |A_qq|), abs_skip) are set to zero
+// instead of rotated (abs_skip: an absolute floor, e.g. the rounding level of
+// the matrix when only its leading eigenpairs are wanted).
 template <int N, bool WANT_U = true>
 __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N],
-                             float tol = 1e-14f) {
+                             float tol = 1e-14f, float abs_skip = 0.f) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -609,7 +612,7 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
         // 1e-10 of the diagonal pair is dropped: a rotation that small
         // changes nothing at single precision
         const float ab = hypotf(b.x, b.y);
-        if (!(ab > 1e-10f * (fabsf(A[p][p].x) + fabsf(A[q][q].x)))) {
+        if (!(ab > fmaxf(1e-10f * (fabsf(A[p][p].x) + fabsf(A[q][q].x)), abs_skip))) {
           A[p][q] = A[q][p] = make_float2(0.f, 0.f);
           continue;
         }

@@ -1,8 +1,9 @@
 // Kernels for stacked passes (Sec. 3: K registered passes as K p channels,
 // rank-K spatial factor).  With p = 6 the p^2 x p^2 Gram M = R R^H has 666
-// complex entries, too many for one thread, so the two steps that hold it run
-// a warp per cell: k_mgram forms M and the block sums of S(i, k) from the
-// exact lag store the moments pass wrote, and k_flipflop_w runs Alg. 2 on M.
+// complex entries, too many for one thread's registers: k_mgram forms M and
+// the block sums of S(i, k) from the exact lag store the moments pass wrote,
+// a warp per cell, and k_flipflop_t runs Alg. 2 with a thread per cell,
+// streaming M from the per-cell arrays.
 // The B / U_B pass (k_bfit) and the projection (k_detect) are the
 // single-pass kernels instantiated for more channels.  k_change forms the
 // per-pass maxima of the statistic and their difference (the noncoherent
@@ -13,7 +14,8 @@
 
 namespace kstap {
 
-constexpr int kWarpCells = 8;   // cells per CTA (one warp each) in k_mgram and k_flipflop_w
+constexpr int kWarpCells = 8;     // cells per CTA (one warp each) in k_mgram
+constexpr int kFlipThreads = 64;  // cells per CTA (one thread each) in k_flipflop_t
 
 // Row J of the Hermitian upper-triangle index: the J with
 // tri_idx(n, J, J) <= e < tri_idx(n, J + 1, J + 1).
@@ -25,34 +27,33 @@ __device__ __forceinline__ void tri_rowcol(int n, int e, int& J, int& K) {
 
 // CTA = one cell row x kWarpCells cells, a warp per cell.  Per lag
 // g = Q-1 .. 0 the tile's lag sums (hi parts of the float-float store) are
-// staged as [position][J]; each lane accumulates its entries of
-// W = sum_j l_g(c + j) l_g(c + j)^H and of the block sums s.  Before lag 0
-// the negative lags are folded in (M += conj(Pi M Pi^T), s += conj(Pi s),
-// Pi swapping the channel pair (i, k) -> (k, i)), as in the single-pass
-// moments kernel.
+// staged as [position][J]; M = sum_g sum_j l_g(c + j) l_g(c + j)^H is
+// accumulated in P x P blocks, lane b < P(P+1)/2 owning block (I, K), I <= K,
+// of the PP x PP Gram (rows J = P I + a, columns P K + b): per position it
+// loads 2P entries of l and does P^2 complex multiply-adds.  The remaining
+// lanes accumulate the block sums s.  Before lag 0 the negative lags are
+// folded in (M += conj(Pi M Pi^T), s += conj(Pi s), Pi swapping the channel
+// pair (i, k) -> (k, i)), as in the single-pass moments kernel.
 template <int P, int Q>
-__global__ void __launch_bounds__(kWarpCells * 32)
+__global__ void __launch_bounds__(kWarpCells * 32, 2)
 k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
         const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NE = PP * (PP + 1) / 2;
-  constexpr int EPL = (NE + 31) / 32;   // M entries per lane
-  constexpr int SPL = (PP + 31) / 32;   // block sums per lane
+  constexpr int NBP = P * (P + 1) / 2;   // blocks of M on and above the diagonal
+  static_assert(NBP < 32 && P % 2 == 0, "a block per lane, 16-byte block rows");
+  constexpr int NSL = 32 - NBP;          // lanes for the block sums
+  constexpr int SPL = (PP + NSL - 1) / NSL;
   constexpr int TCm = kWarpCells;
   constexpr int NUmax = TCm + Q - 1;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* Ls = reinterpret_cast<float2*>(smem);                 // [NUmax][PP]
-  float2* Ft = Ls + NUmax * PP;                                 // [warps][NE] fold scratch
-  float2* Fs = Ft + kWarpCells * NE;                            // [warps][PP]
+  float2* Ft = Ls + NUmax * PP;                                 // [warps][PP][PP] fold scratch
+  float2* Fs = Ft + kWarpCells * PP * PP;                       // [warps][PP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int ejk[EPL];                                                 // (J | K << 8) of each entry
-#pragma unroll
-  for (int t = 0; t < EPL; ++t) {
-    const int e = lane + 32 * t;
-    int J = 0, K = 0;
-    if (e < NE) tri_rowcol(PP, e, J, K);
-    ejk[t] = J | (K << 8);
-  }
+  const bool mlane = lane < NBP;
+  int bI = 0, bK = 0;
+  if (mlane) tri_rowcol(P, lane, bI, bK);
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindMgram]; tile += gridDim.x) {
     int lt;
     const Job& JB = job_of(JL, kKindMgram, tile, lt);
@@ -63,11 +64,14 @@ k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     const int cl = warp;
     const bool live = c0 + cl < g.W;
     const int WL = g.W + Q - 1;
-    float2 acc[EPL], sacc[SPL];
+    float2 acc[P][P], sacc[SPL];
 #pragma unroll
-    for (int t = 0; t < EPL; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) acc[a][b] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < SPL; ++t) sacc[t] = make_float2(0.f, 0.f);
+#pragma unroll 1
     for (int lagg = Q - 1; lagg >= 0; --lagg) {
       const int NU = TCm + Q - 1 - lagg;
       const float4* src = Lw + ((size_t)r * Q + lagg) * PP * WL;
@@ -79,45 +83,78 @@ k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
       }
       __syncthreads();
       if (lagg == 0) {
-        // fold the negative lags into the sums over g > 0
-        float2* ft = Ft + warp * NE;
+        // fold the negative lags into the sums over g > 0.  The whole
+        // Hermitian W goes to shared memory; Pi maps entry (a, b) of block
+        // (I, K) to entry (I, K) of block (a, b), so each lane reads its
+        // partners at fixed offsets from one base.
+        float2* ft = Ft + warp * PP * PP;
         float2* fs = Fs + warp * PP;
+        if (mlane) {
 #pragma unroll
-        for (int t = 0; t < EPL; ++t)
-          if (lane + 32 * t < NE) ft[lane + 32 * t] = acc[t];
+          for (int a = 0; a < P; ++a)
 #pragma unroll
-        for (int t = 0; t < SPL; ++t)
-          if (lane + 32 * t < PP) fs[lane + 32 * t] = sacc[t];
-        __syncwarp();
+            for (int b = 0; b < P; ++b) {
+              const int J = P * bI + a, K = P * bK + b;
+              if (bI == bK && a > b) continue;
+              ft[J * PP + K] = acc[a][b];
+              ft[K * PP + J] = cconj(acc[a][b]);
+            }
+        } else {
 #pragma unroll
-        for (int t = 0; t < EPL; ++t) {
-          if (lane + 32 * t >= NE) continue;
-          const int J = ejk[t] & 255, K = ejk[t] >> 8;
-          const int a = (J % P) * P + J / P, b = (K % P) * P + K / P;   // Pi J, Pi K
-          const float2 w = (a <= b) ? ft[tri_idx(PP, a, b)] : cconj(ft[tri_idx(PP, b, a)]);
-          acc[t] = cadd(acc[t], cconj(w));
+          for (int t = 0; t < SPL; ++t) {
+            const int J = (lane - NBP) + NSL * t;
+            if (J < PP) fs[J] = sacc[t];
+          }
         }
+        __syncwarp();
+        if (mlane) {
+          const float2* fp = ft + bI * PP + bK;   // W[P a + I][P b + K] = fp[a P PP + b P]
 #pragma unroll
-        for (int t = 0; t < SPL; ++t) {
-          const int J = lane + 32 * t;
-          if (J >= PP) continue;
-          sacc[t] = cadd(sacc[t], cconj(fs[(J % P) * P + J / P]));
+          for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+              if (bI == bK && a > b) continue;
+              acc[a][b] = cadd(acc[a][b], cconj(fp[a * P * PP + b * P]));
+            }
+        } else {
+#pragma unroll
+          for (int t = 0; t < SPL; ++t) {
+            const int J = (lane - NBP) + NSL * t;
+            if (J < PP) sacc[t] = cadd(sacc[t], cconj(fs[(J % P) * P + J / P]));
+          }
         }
         __syncwarp();
       }
       if (live) {
+#pragma unroll 1
         for (int j = 0; j < Q - lagg; ++j) {
           const float2* l = Ls + (cl + j) * PP;
+          if (mlane) {
+            float2 x[P], y[P];
+            const float4* lx = reinterpret_cast<const float4*>(l + P * bI);
+            const float4* ly = reinterpret_cast<const float4*>(l + P * bK);
 #pragma unroll
-          for (int t = 0; t < EPL; ++t) {
-            if (lane + 32 * t >= NE) continue;
-            const float2 x = l[ejk[t] & 255], y = l[ejk[t] >> 8];
-            acc[t].x += x.x * y.x + x.y * y.y;   // l[J] conj(l[K])
-            acc[t].y += x.y * y.x - x.x * y.y;
+            for (int h = 0; h < P / 2; ++h) {
+              const float4 v = lx[h], w = ly[h];
+              x[2 * h] = make_float2(v.x, v.y);
+              x[2 * h + 1] = make_float2(v.z, v.w);
+              y[2 * h] = make_float2(w.x, w.y);
+              y[2 * h + 1] = make_float2(w.z, w.w);
+            }
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+              for (int b = 0; b < P; ++b) {   // l[J] conj(l[K])
+                acc[a][b].x += x[a].x * y[b].x + x[a].y * y[b].y;
+                acc[a][b].y += x[a].y * y[b].x - x[a].x * y[b].y;
+              }
+          } else {
+#pragma unroll
+            for (int t = 0; t < SPL; ++t) {
+              const int J = (lane - NBP) + NSL * t;
+              if (J < PP) sacc[t] = cadd(sacc[t], l[J]);
+            }
           }
-#pragma unroll
-          for (int t = 0; t < SPL; ++t)
-            if (lane + 32 * t < PP) sacc[t] = cadd(sacc[t], l[lane + 32 * t]);
         }
       }
       __syncthreads();
@@ -125,187 +162,215 @@ k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     if (live) {
       const size_t ncell = (size_t)JL.NC;
       const size_t cell = (size_t)JB.cell0 + (size_t)r * g.W + (c0 + cl);
+      if (mlane) {
 #pragma unroll
-      for (int t = 0; t < EPL; ++t)
-        if (lane + 32 * t < NE) Mw[(size_t)(lane + 32 * t) * ncell + cell] = acc[t];
+        for (int a = 0; a < P; ++a)
 #pragma unroll
-      for (int t = 0; t < SPL; ++t)
-        if (lane + 32 * t < PP) Sw[(size_t)(lane + 32 * t) * ncell + cell] = sacc[t];
+          for (int b = 0; b < P; ++b) {
+            const int J = P * bI + a, K = P * bK + b;
+            if (J <= K) Mw[(size_t)tri_idx(PP, J, K) * ncell + cell] = acc[a][b];
+          }
+      } else {
+#pragma unroll
+        for (int t = 0; t < SPL; ++t) {
+          const int J = (lane - NBP) + NSL * t;
+          if (J < PP) Sw[(size_t)J * ncell + cell] = sacc[t];
+        }
+      }
     }
   }
 }
 
-// Alg. 2 on M with a warp per cell (see k_flipflop for the single-pass form):
-// y = M a by rows over the lanes, the rank-r_a truncation of the P x P
-// Hermitian A~ by a Jacobi sweep in lane 0, the stop rule
-// |a_k+1 - a_k| <= eps |a_k+1|, eta from the closed form with float-float sums.
+// Alg. 2 on M with a thread per cell (the single-pass kernel k_flipflop holds
+// M in registers; here the 666 entries of M are streamed from the per-cell
+// arrays each iteration, coalesced over the cells of a warp, and each entry
+// serves both y_J += M_JK a_K and y_K += conj(M_JK) a_J).  The thread's a, y
+// and leading eigenvectors sit in shared memory ([entry][thread], so the
+// lanes of a warp hit distinct banks) and the loops over them stay rolled:
+// a fully unrolled 36 x 36 product does not fit the instruction cache.  The
+// rank-r_a truncation of the P x P Hermitian A~ = vec^-1(y) |a|^2 / a^H M a
+// is a cyclic Jacobi in registers whose off-diagonal entries below the
+// rounding level of the matrix are dropped, not rotated (only the leading
+// r_a eigenpairs are used).  Stop rule |a_k+1 - a_k| <= eps |a_k+1|; eta from
+// the closed form with float-float sums, as in k_flipflop.
 template <int P>
-__global__ void __launch_bounds__(kWarpCells * 32)
-k_flipflop_w(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __restrict__ Sw,
+__global__ void __launch_bounds__(kFlipThreads)
+k_flipflop_t(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __restrict__ Sw,
              float2* __restrict__ aw) {
   constexpr int PP = P * P;
-  constexpr int NE = PP * (PP + 1) / 2;
-  constexpr int RPL = (PP + 31) / 32;   // rows of M per lane
+  constexpr int RA = 2;                             // largest r_a of this route
+  constexpr int nt = kFlipThreads;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* Mt = reinterpret_cast<float2*>(smem) + warp * (NE + 3 * PP);
-  float2* as = Mt + NE;          // a
-  float2* ys = as + PP;          // y = M a
-  float2* an_ = ys + PP;         // next a
-  __shared__ int done_w[kWarpCells];
-  __shared__ float2 UAw[kWarpCells][P * P];
-  __shared__ float dw[kWarpCells][P];
+  float2* as = reinterpret_cast<float2*>(smem);     // [PP][nt] a
+  float2* ys = as + PP * nt;                        // [PP][nt] y = M a
+  float2* Ut = ys + PP * nt;                        // [P RA][nt] leading eigenvectors
   const size_t ncell = (size_t)JL.NC;
-  const Geom& g = g0;
-  const int ra = g.r_a;
+  const int tid = threadIdx.x;
+  float2* a_ = as + tid;
+  float2* y_ = ys + tid;
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindFlip]; tile += gridDim.x) {
-    int lt;
-    const Job& JB = job_of(JL, kKindFlip, tile, lt);
-    const size_t local = (size_t)lt * kWarpCells + warp;
-    if (local >= (size_t)JB.H * JB.W) continue;   // warp-uniform
-    const size_t cell = (size_t)JB.cell0 + local;
-    for (int e = lane; e < NE; e += 32) Mt[e] = Mw[(size_t)e * ncell + cell];
-    for (int J = lane; J < PP; J += 32) as[J] = Sw[(size_t)J * ncell + cell];
-    __syncwarp();
-    for (int J = lane; J < PP; J += 32) {   // a_0 ~ block sums of S, Hermitised
+  int lt;
+  const Job& JB = job_of(JL, kKindFlip, tile, lt);
+  const Geom& g = g0;
+  const size_t local = (size_t)lt * nt + tid;
+  if (local >= (size_t)JB.H * JB.W) continue;
+  const size_t cell = (size_t)JB.cell0 + local;
+  const float2* __restrict__ Mc = Mw + cell;        // entry e at Mc[e ncell]
+  // a_0 = R 1 / q^2 is proportional to the sum of S's block entries; Hermitise.
+#pragma unroll 1
+  for (int J = 0; J < PP; ++J) {
+    const int i = J % P, k = J / P;
+    const float2 x = Sw[J * ncell + cell], z = Sw[(k + P * i) * ncell + cell];
+    a_[J * nt] = make_float2(0.5f * (x.x + z.x), 0.5f * (x.y - z.y));
+  }
+  const int ra = g.r_a;
+  // the leading r_a eigenpairs of the last truncation (identity columns and
+  // zeros for a cell whose first iterate is degenerate)
+  float dt[RA];
+#pragma unroll
+  for (int m = 0; m < RA; ++m) {
+    dt[m] = 0.f;
+#pragma unroll
+    for (int i = 0; i < P; ++i) Ut[(i * RA + m) * nt + tid] = make_float2(i == m ? 1.f : 0.f, 0.f);
+  }
+  int it = 0;
+  const float tol2 = g.eps * g.eps;
+  float dn_prev = kFltMax;
+  for (it = 1; it <= g.max_iter; ++it) {
+#pragma unroll 1
+    for (int J = 0; J < PP; ++J) y_[J * nt] = make_float2(0.f, 0.f);
+    const float2* mp = Mc;
+    float an = 0.f, aMa = 0.f;
+#pragma unroll 1
+    for (int J = 0; J < PP; ++J) {
+      const float2 aJ = a_[J * nt];
+      float2 yJ = cadd(y_[J * nt], cmul(__ldg(mp), aJ));   // diagonal (real) entry
+      mp += ncell;
+#pragma unroll 4
+      for (int K = J + 1; K < PP; ++K) {   // upper-triangle order
+        const float2 m = __ldg(mp);
+        mp += ncell;
+        yJ = cadd(yJ, cmul(m, a_[K * nt]));
+        y_[K * nt] = cadd(y_[K * nt], cmulc(m, aJ));
+      }
+      y_[J * nt] = yJ;
+      an += cabs2(aJ);
+      aMa += aJ.x * yJ.x + aJ.y * yJ.y;
+    }
+    if (!(aMa > 0.f) || !(an > 0.f)) break;
+    const float f = an / aMa;
+    float2 At[P][P];
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const float2 x = y_[(i + P * k) * nt], z = y_[(k + P * i) * nt];
+        At[i][k] = make_float2(0.5f * f * (x.x + z.x), 0.5f * f * (x.y - z.y));
+        if (i == k) tr += fabsf(At[i][i].x);
+      }
+    float d[P];
+    float2 U[P][P];
+    jacobi_small<P>(At, d, U, 1e-14f, 3e-8f * tr);
+#pragma unroll
+    for (int m = 0; m < RA; ++m) {
+      dt[m] = d[m];
+#pragma unroll
+      for (int i = 0; i < P; ++i) Ut[(i * RA + m) * nt + tid] = U[i][m];
+    }
+    // a_k+1 = sum_{m < r_a} d_m u_m u_m^H over a_k in place, and the stop rule
+    float dn = 0.f, nn = 0.f;
+#pragma unroll 1
+    for (int J = 0; J < PP; ++J) {
       const int i = J % P, k = J / P;
-      const float2 x = as[i + P * k], y = as[k + P * i];
-      an_[J] = make_float2(0.5f * (x.x + y.x), 0.5f * (x.y - y.y));
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < RA; ++m)
+        if (m < ra)
+          s = cadd(s, cscale(cmul(Ut[(i * RA + m) * nt + tid], cconj(Ut[(k * RA + m) * nt + tid])),
+                             dt[m]));
+      dn += cabs2(csub(s, a_[J * nt]));
+      nn += cabs2(s);
+      a_[J * nt] = s;
     }
-    __syncwarp();
-    for (int J = lane; J < PP; J += 32) as[J] = an_[J];
-    __syncwarp();
-    const float tol2 = g.eps * g.eps;
-    int it = 0;
-    if (lane == 0) {
-      done_w[warp] = 0;
-      for (int i = 0; i < P; ++i) {     // factors of a cell whose first iterate is degenerate
-        dw[warp][i] = 0.f;
-        for (int m = 0; m < P; ++m) UAw[warp][i * P + m] = make_float2(i == m ? 1.f : 0.f, 0.f);
-      }
-    }
-    __syncwarp();
-    for (it = 1; it <= g.max_iter; ++it) {
-      float an = 0.f, aMa = 0.f;
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        const int J = lane + 32 * t;
-        if (J >= PP) continue;
-        float2 s = make_float2(0.f, 0.f);
-        for (int K = 0; K < PP; ++K) {
-          const float2 m = (J <= K) ? Mt[tri_idx(PP, J, K)] : cconj(Mt[tri_idx(PP, K, J)]);
-          s = cadd(s, cmul(m, as[K]));
-        }
-        ys[J] = s;
-        an += cabs2(as[J]);
-        aMa += as[J].x * s.x + as[J].y * s.y;
-      }
-      an = warp_sum(an);
-      aMa = warp_sum(aMa);
-      if (!(aMa > 0.f) || !(an > 0.f)) break;   // warp-uniform
-      __syncwarp();
-      if (lane == 0) {
-        const float f = an / aMa;
-        float2 At[P][P], U[P][P];
-        float d[P];
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-#pragma unroll
-          for (int k = 0; k < P; ++k) {
-            const float2 x = ys[i + P * k], z = ys[k + P * i];
-            At[i][k] = make_float2(0.5f * f * (x.x + z.x), 0.5f * f * (x.y - z.y));
-          }
-        jacobi_small<P>(At, d, U);
-        float dn = 0.f, nn = 0.f;
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-#pragma unroll
-          for (int k = 0; k < P; ++k) {
-            float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int m = 0; m < P; ++m)
-              if (m < ra) s = cadd(s, cscale(cmul(U[i][m], cconj(U[k][m])), d[m]));
-            dn += cabs2(csub(s, as[i + P * k]));
-            nn += cabs2(s);
-            an_[i + P * k] = s;
-          }
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          dw[warp][i] = d[i];
-#pragma unroll
-          for (int m = 0; m < P; ++m) UAw[warp][i * P + m] = U[i][m];
-        }
-        done_w[warp] = dn <= tol2 * nn;
-      }
-      __syncwarp();
-      for (int J = lane; J < PP; J += 32) as[J] = an_[J];
-      __syncwarp();
-      if (done_w[warp]) break;
-    }
-    const bool noconv = it > g.max_iter;
-    if (noconv) it = g.max_iter;
-    if (JL.report && lane == 0) count_lanes(JL.report, noconv);
-    // eta^2 = 1 - a^H M a / (|a|^2 tr M), float-float sums over the lanes' rows
-    float trs = 0.f, trc = 0.f, ans = 0.f, anc = 0.f, qs = 0.f, qc = 0.f;
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      const int J = lane + 32 * t;
-      if (J >= PP) continue;
-      const float dM = Mt[tri_idx(PP, J, J)].x;
-      float tt, e;
-      two_sum(trs, dM, tt, e);
-      trs = tt;
+    if (dn <= tol2 * nn) break;
+    // rounding floor: once |a_k+1 - a_k| <= 1e-4 |a_k+1|, a step that no
+    // longer shrinks means the single-precision truncation has stopped
+    // improving the iterate (cells whose leading spatial eigenvalues are
+    // close); further iterations only move it within that floor
+    if (dn <= 1e-8f * nn && dn >= dn_prev) break;
+    dn_prev = dn;
+  }
+  const bool noconv = it > g.max_iter;
+  if (noconv) it = g.max_iter;
+  if (JL.report) count_lanes(JL.report, noconv);
+  // cells whose box holds a NaN / Inf sample: iters = -1, eta = NaN
+  bool bad = false;
+  if (JB.maxbits && JB.maxbits[1]) {
+    Geom gj = with_job(g0, JB);
+    bad = box_nonfinite(JB.Y, gj, (int)(local / JB.W), (int)(local % JB.W), 0, 1);
+    if (JL.report) count_lanes(JL.report + 1, bad);
+  }
+  // eta^2 = 1 - a^H M a / (|a|^2 tr M), the three sums in float-float
+  float trs = 0.f, trc = 0.f, ans = 0.f, anc = 0.f, qs = 0.f, qc = 0.f;
+  {
+    const float2* mp = Mc;
+#pragma unroll 1
+    for (int J = 0; J < PP; ++J) {
+      const float2 aJ = a_[J * nt];
+      aw[J * ncell + cell] = aJ;
+      const float dM = __ldg(mp).x;
+      mp += ncell;
+      float t, e;
+      two_sum(trs, dM, t, e);
+      trs = t;
       trc = __fadd_rn(trc, e);
       float p1, pe;
-      two_prod(as[J].x, as[J].x, p1, pe);
+      two_prod(aJ.x, aJ.x, p1, pe);
       acc_ffxf(ans, anc, p1, pe, 1.f);
       acc_ffxf(qs, qc, p1, pe, dM);
-      two_prod(as[J].y, as[J].y, p1, pe);
+      two_prod(aJ.y, aJ.y, p1, pe);
       acc_ffxf(ans, anc, p1, pe, 1.f);
       acc_ffxf(qs, qc, p1, pe, dM);
+#pragma unroll 2
       for (int K = J + 1; K < PP; ++K) {   // 2 Re(conj(a_J) M_JK a_K)
-        const float2 m = Mt[tri_idx(PP, J, K)];
+        const float2 m = __ldg(mp);
+        const float2 aK = a_[K * nt];
+        mp += ncell;
         float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
-        acc_prod(rs, rc, m.x, as[K].x);
-        acc_prod(rs, rc, -m.y, as[K].y);
-        acc_prod(is, ic, m.x, as[K].y);
-        acc_prod(is, ic, m.y, as[K].x);
-        acc_ffxf(qs, qc, rs, rc, 2.f * as[J].x);
-        acc_ffxf(qs, qc, is, ic, 2.f * as[J].y);
+        acc_prod(rs, rc, m.x, aK.x);
+        acc_prod(rs, rc, -m.y, aK.y);
+        acc_prod(is, ic, m.x, aK.y);
+        acc_prod(is, ic, m.y, aK.x);
+        acc_ffxf(qs, qc, rs, rc, 2.f * aJ.x);
+        acc_ffxf(qs, qc, is, ic, 2.f * aJ.y);
       }
     }
-    const ff trf = ff_warp_sum(ff_make(trs, trc)), anf = ff_warp_sum(ff_make(ans, anc));
-    const ff qf = ff_warp_sum(ff_make(qs, qc));
-    for (int J = lane; J < PP; J += 32) aw[(size_t)J * ncell + cell] = as[J];
-    // cells whose box holds a NaN / Inf sample: iters = -1, eta = NaN
-    bool bad = false;
-    if (JB.maxbits && JB.maxbits[1]) {
-      const Geom gj = with_job(g0, JB);
-      bad = box_nonfinite(JB.Y, gj, (int)(local / JB.W), (int)(local % JB.W), lane, 32);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-      if (JL.report && lane == 0) count_lanes(JL.report + 1, bad);
-    }
-    if (lane == 0) {
-      float trA = 0.f;
-#pragma unroll
-      for (int m = 0; m < P; ++m)
-        if (m < ra) trA += dw[warp][m];
-      const float sc = (trA != 0.f) ? (float)P / trA : 1.f;
-      for (int i = 0; i < P; ++i)
-        for (int m = 0; m < ra; ++m) JB.UA[(local * P + i) * ra + m] = UAw[warp][i * P + m];
-      if (JB.lamA)
-        for (int m = 0; m < ra; ++m) JB.lamA[local * ra + m] = dw[warp][m] * sc;
-      if (JB.iters) JB.iters[local] = bad ? -1 : it;
-      if (JB.eta) {
-        const double tr = (double)trf.hi + trf.lo, an = (double)anf.hi + anf.lo;
-        const double aMa = (double)qf.hi + qf.lo;
-        const double e2 = (tr > 0.0 && an > 0.0) ? 1.0 - aMa / (an * tr) : 0.0;
-        JB.eta[local] = bad ? __int_as_float(0x7fc00000) : (float)sqrt(e2 > 0.0 ? e2 : 0.0);
-      }
-    }
-    __syncwarp();
   }
+  const double tr = (double)trs + (double)trc;
+  const double an = (double)ans + (double)anc;
+  const double aMa = (double)qs + (double)qc;
+  float trA = 0.f;
+#pragma unroll
+  for (int m = 0; m < RA; ++m)
+    if (m < ra) trA += dt[m];
+  const float sc = (trA != 0.f) ? (float)P / trA : 1.f;
+#pragma unroll
+  for (int i = 0; i < P; ++i)
+#pragma unroll
+    for (int m = 0; m < RA; ++m)
+      if (m < ra) JB.UA[(local * P + i) * ra + m] = Ut[(i * RA + m) * nt + tid];
+  if (JB.lamA) {
+#pragma unroll
+    for (int m = 0; m < RA; ++m)
+      if (m < ra) JB.lamA[local * ra + m] = dt[m] * sc;
+  }
+  if (JB.iters) JB.iters[local] = bad ? -1 : it;
+  if (JB.eta) {
+    const double e2 = (tr > 0.0 && an > 0.0) ? 1.0 - aMa / (an * tr) : 0.0;
+    JB.eta[local] = bad ? __int_as_float(0x7fc00000) : (float)sqrt(e2 > 0.0 ? e2 : 0.0);
+  }
+  }  // tile loop
 }
 
 // Per cell: Tmax_k = max over the V velocities of pass k of T_all (K V per
