@@ -223,12 +223,12 @@ def work_per_cell(wl):
 # source it was taken on: the bench reports null once the file changes.
 KERNEL_SRC = os.path.join(ROOT, "paper_1604_03622_b300", "csrc", "kstap_kernels.cuh")
 TRAFFIC = {
-    # 512 x 1024-cell capture (1.263 GB read + 0.387 GB write) x 2 for the 1024^2
+    # 512 x 1024-cell capture (1.264 GB read + 0.387 GB write) x 2 for the 1024^2
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.263e9 + 0.387e9),
-        sha256="8f7a20782e98f626ad6ca34eaafb5b208654fc7d5acfd2bb8e200ee1d2c48f95",
+        bytes=2 * (1.263921e9 + 0.387137e9),
+        sha256="2af87376425e87b5c2a9af884af8c5afb8f18a517fdaed5d8dcafca67c38356e",
         source="profiles/frame1024_512x1024_kernels.md"),
 }
 
