@@ -128,6 +128,56 @@ def test_lrkron_exact_recovery_from_kronecker_data():
     np.testing.assert_allclose(PA, np.outer(h, h.conj()) / np.vdot(h, h).real, atol=1e-12)
 
 
+def test_lrkron_stacked_passes_exact_recovery():
+    """Sec. 3 multipass: two passes stacked as p = 6 channels.  Snapshots
+    a_s v_t^T over all pairs, with spatial vectors [h1; 0], [0; h2] and a mix
+    (rank-2 A), give S = A (x) B exactly; r_a = 2 recovers it (eta = 0) and
+    P_A is the projector onto span{[h1; 0], [0; h2]}."""
+    rng = np.random.default_rng(16)
+    p1, q, r_b = 3, 6, 2
+    h1, h2 = crandn(rng, p1), crandn(rng, p1)
+    z = np.zeros(p1, complex)
+    avs = [np.concatenate([h1, z]), np.concatenate([z, h2]), 0.5j * np.concatenate([h1, h2])]
+    vs = crandn(rng, r_b, q)
+    X = np.stack([np.outer(a, v) for a in avs for v in vs])
+    S = oracle.scm(X)
+    out = oracle.lrkron(S, 2 * p1, q, 2, r_b)
+    np.testing.assert_allclose(np.kron(out["A"], out["B"]), S, atol=1e-11 * abs(S).max())
+    assert out["eta"] < 1e-11
+    PA = out["UA"] @ out["UA"].conj().T
+    E = np.stack([avs[0], avs[1]], axis=1)
+    Q_, _ = np.linalg.qr(E)
+    np.testing.assert_allclose(PA, Q_ @ Q_.conj().T, atol=1e-11)
+    # with r_a = 1 the rank-2 spatial factor cannot be represented: eta > 0
+    assert oracle.lrkron(S, 2 * p1, q, 1, r_b)["eta"] > 1e-3
+
+
+def test_stacked_bank_measures_each_pass():
+    """Sec. 8: with the stacked bank (entry k V + v = a_v on pass k's channels),
+    a target present only in pass 1 and orthogonal to both clutter factors
+    gives T = |beta|^2 |d|^2 on its pass-1 entry (Sec. 6, projector = I on d)
+    and 0 on its pass-0 entry (the two steering vectors are orthogonal)."""
+    p1, q, V = 3, 8, 8
+    ba, bb = gen.steering_bank(p1, q, V)
+    bank_a = np.zeros((2 * V, 2 * p1), complex)
+    bank_b = np.zeros((2 * V, q), complex)
+    for k in range(2):
+        bank_a[k * V:(k + 1) * V, k * p1:(k + 1) * p1] = ba
+        bank_b[k * V:(k + 1) * V] = bb
+    v, beta = 5, 0.8 - 0.3j
+    d1 = np.kron(bank_a[V + v], bank_b[V + v])                  # pass-1 steering, vec(X^T)
+    X = beta * np.outer(bank_a[V + v], bank_b[V + v])
+    # clutter factors orthogonal to the target: U_A on pass 0 only, U_B
+    # orthogonal to b_v
+    UA = np.concatenate([ba[1], np.zeros(p1)])[:, None] / np.sqrt(p1)
+    w = bb[2] - bb[v] * np.vdot(bb[v], bb[2]) / np.vdot(bb[v], bb[v])
+    UB = (w / np.linalg.norm(w))[:, None]
+    T, _ = oracle.stat(X, UA, UB, bank_a, bank_b)
+    np.testing.assert_allclose(T[V + v], abs(beta) ** 2 * np.vdot(d1, d1).real, rtol=1e-12)
+    assert abs(T[v]) < 1e-20
+    assert T.argmax() == V + v
+
+
 def test_lrkron_exact_recovery_given_S():
     rng = np.random.default_rng(7)
     p, q = 3, 5
