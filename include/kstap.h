@@ -63,9 +63,10 @@ typedef enum {
  * pulses (azimuth window), ranks r_a, r_b of A and B (Eq. SparseOpt), Alg. 2
  * tolerance eps and iteration cap, detection threshold tau on Tmax.
  * Limits of this build: p == 3 with q in {8, 16, 32} and r_a == 1 (the
- * paper's rank-one spatial model, Eq. KronCov); or p == 6 -- K = 2 registered
- * passes of 3 channels stacked as one frame (Sec. 3), spatial rank r_a in
- * {1, 2} -- with q in {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
+ * paper's rank-one spatial model, Eq. KronCov) or r_a == 2 (KSTAP_FP32 bank
+ * and Kron-STAP filter); or p == 6 -- K = 2 registered passes of 3 channels
+ * stacked as one frame (Sec. 3), spatial rank r_a in {1, 2} -- with q in
+ * {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
  * 1 <= r_b <= 4 with r_b < q (Sec. 5 warns against r_b close to q),
  * ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1) <= 1024, and a
  * training box whose tiles fit shared memory.  Other values give

@@ -151,8 +151,12 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "q must be 8, 16 or 32";
     return false;
   }
-  if (p->p == 3 && p->r_a != 1) {
-    why = "r_a must be 1 for p == 3 (rank-one spatial clutter model)";
+  if (p->r_a < 1 || p->r_a > 2) {
+    why = "r_a must be 1 (rank-one spatial clutter model) or 2";
+    return false;
+  }
+  if (p->r_a == 2 && (p->precision != KSTAP_FP32 || p->filter != KSTAP_FILTER_KRON)) {
+    why = "r_a == 2 runs on the KSTAP_FP32 bank with the Kron-STAP filter";
     return false;
   }
   if (p->p == 6 && (p->q > 16 || p->r_a < 1 || p->r_a > 2 || p->precision != KSTAP_FP32 ||
@@ -564,13 +568,12 @@ template <int P, int Q, int R>
 kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                             int sm_count, int waves, cudaStream_t s) {
   if (JL.njobs < 1) return KSTAP_OK;
+  if (g.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
   if constexpr (P <= 3) {
     if (ctx->prm.precision == KSTAP_FP16X3)
       return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
     if (ctx->prm.precision == KSTAP_BF16X3)
       return enqueue_detect_tc<P, Q, R, true>(ctx, prof, g, JL, sm_count, waves, s);
-  } else {
-    if (ctx->prm.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
   }
   return enqueue_detect_fp32<P, Q, R, 1>(ctx, prof, g, JL, sm_count, waves, s);
 }

@@ -34,7 +34,9 @@ def test_create_rejects_unsupported_parameters_without_gpu():
     bad = [
         K.make_params(4, 16, 1, 3, 4, 7, 1, 2, 10.0),    # p != 3
         K.make_params(3, 12, 1, 3, 4, 7, 1, 2, 10.0),    # q not in {8,16,32}
-        K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0),    # r_a != 1
+        K.make_params(3, 16, 3, 3, 4, 7, 1, 2, 10.0),    # r_a > 2
+        K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0, precision="fp16x3"),   # r_a = 2: FP32 bank
+        K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0, filter="classical"),   # r_a = 2: Kron filter
         K.make_params(3, 8, 1, 8, 3, 4, 1, 2, 10.0),     # r_b >= q (Sec. 5)
         K.make_params(3, 16, 1, 5, 4, 7, 1, 2, 10.0),    # r_b > 4
         K.make_params(3, 16, 1, 3, 1, 7, 2, 2, 10.0),    # guard > ring

@@ -64,6 +64,22 @@ def test_parity_every_rank_variant(name, r_b):
     assert np.abs(PB - ref["PB"]).max() < 1e-8
 
 
+@pytest.mark.parametrize("name,H,W", [("small64", 20, 43), ("frame1024", 12, 37),
+                                      ("precision2048", 5, 21)])
+def test_parity_spatial_rank_two(name, H, W):
+    """r_a = 2 on the single-pass frame (rank-2 U_A in Alg. 2 and the
+    projector; the synthetic A is full-rank Toeplitz, eigenvalue gap ~2)."""
+    wl = _wl(name, H, W, r_a=2)
+    f = gen.make_frame(wl)
+    ref = oracle.run_workload(f)
+    gpu = run_gpu(f)
+    compare(gpu, ref, np.arange(wl.H * wl.W), wl.tau)
+    PA = projector(gpu["UA"])
+    assert gpu["UA"].shape[-1] == 2
+    assert np.abs(PA - ref["PA"]).max() < 1e-4
+    np.testing.assert_allclose(gpu["lamA"], ref["lamA"], rtol=1e-4)
+
+
 def test_parity_rank_one_temporal_and_single_cell():
     wl = _wl("small64", 1, 1, r_b=1)
     f = gen.make_frame(wl)
