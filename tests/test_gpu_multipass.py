@@ -161,3 +161,52 @@ def test_stacked_pass_nonfinite_sample():
     assert len(ok) > 0
     ref = _oracle(f, 2, cells=ok)
     compare(gpu, ref, ok, wl.tau)
+
+
+def test_stacked_pass_batch_strips_and_serving():
+    """The stacked-pass context on the batch, strip and serving paths: a batch
+    of uneven frames is bit-identical to the frames run one by one; a budget
+    a third of the whole workspace runs the frame as row strips (their own
+    fixed-point scale: equal to the unsplit frame to 1e-4); a served frame
+    equals the frame run alone."""
+    import torch
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    from gpu_common import t_err
+    from test_gpu_serving import _served
+    sizes = [(9, 30), (1, 1), (14, 17)]
+    frames = [_frame("frame1024", H, W, seed_shift=k) for k, (H, W) in enumerate(sizes)]
+    f0 = frames[0]
+    wl = f0.wl
+    mk = lambda **kw: KStap(6, wl.q, 2, wl.r_b, wl.ring_r, wl.ring_a, wl.guard_r, wl.guard_a,
+                            wl.tau, f0.bank_a, f0.bank_b, **kw)
+    keys = ("Tmax", "vidx", "map", "UA", "UB_hi", "UB_lo", "T_all", "lamA", "eta", "iters")
+    ks = mk()
+    Ys = [torch.from_numpy(f.Y).cuda() for f in frames]
+    alone = [{k: v.cpu().numpy() for k, v in ks.run(Y, T_all=True).items() if k in keys}
+             for Y in Ys]
+    bufs = [ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
+    K.kstap_run_batch(ks.ctx, [ks.frame_desc(Y, b) for Y, b in zip(Ys, bufs)])
+    torch.cuda.synchronize()
+    for r, b in zip(alone, bufs):
+        for k in keys:
+            assert np.array_equal(b[k].cpu().numpy(), r[k]), k
+    tk = K.kstap_submit(ks.ctx, Ys[2], Ys[2].shape[1], Ys[2].shape[2])
+    res = K.kstap_poll(ks.ctx, tk, timeout_us=-1)
+    served = _served(K, ks, Ys[2], res)
+    for k in ("Tmax", "vidx", "map"):
+        assert np.array_equal(served[k], alone[2][k]), k
+    K.kstap_release(ks.ctx, tk)
+    ks.close()
+    # row strips under a small budget
+    big = _frame("frame1024", 41, 33, seed_shift=5)
+    prm = K.make_params(6, wl.q, 2, wl.r_b, wl.ring_r, wl.ring_a, wl.guard_r, wl.guard_a, wl.tau)
+    whole = K.kstap_workspace_bytes(prm, big.wl.H_in, big.wl.W_in)
+    Y = torch.from_numpy(big.Y).cuda()
+    ks0 = mk()
+    ref = ks0.run(Y, T_all=True)["T_all"].cpu().numpy()
+    ks0.close()
+    ks = mk(hbm_budget_bytes=whole // 3)
+    got = ks.run(Y, T_all=True)["T_all"].cpu().numpy()
+    ks.close()
+    assert t_err(got, ref.astype(np.float64)).max() <= 1e-4
