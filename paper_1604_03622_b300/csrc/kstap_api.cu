@@ -271,7 +271,7 @@ int tiles_flip(int H, int W, int p = 3) {
   return (int)(((size_t)H * W + per - 1) / per);
 }
 int tiles_mgram(int H, int W, int p) {
-  return p <= 3 ? 0 : ((W + kstap::kWarpCells - 1) / kstap::kWarpCells) * H;
+  return p <= 3 ? 0 : ((W + kstap::kStrip - 1) / kstap::kStrip) * H;   // a CTA per strip
 }
 int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
 int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
@@ -386,9 +386,10 @@ size_t smem_moments(const Geom& g) {
 }
 
 size_t smem_mgram(const Geom& g) {
-  const size_t PP = (size_t)g.p * g.p;
-  const size_t NUmax = kstap::kWarpCells + g.q - 1;
-  return (NUmax * PP + kstap::kWarpCells * (PP * PP + PP)) * 8;
+  // the lag windows' ring (sum_g (q - g + 1) slots of PP entries), the fold
+  // scratch and the block sums
+  const size_t PP = (size_t)g.p * g.p, slots = (size_t)g.q * (g.q + 3) / 2;
+  return (slots * PP + PP * PP + PP) * 8;
 }
 
 size_t smem_flipt(const Geom& g) {
@@ -508,11 +509,11 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
     const size_t smg = smem_mgram(g);
     KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_mgram<P, Q>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
-    const int gm = grid_for(kstap::k_mgram<P, Q>, kstap::kWarpCells * 32, smg,
-                            JL.ntiles[kstap::kKindMgram], sm_count, waves);
+    const int gm = grid_for(kstap::k_mgram<P, Q>, 64, smg, JL.ntiles[kstap::kKindMgram],
+                            sm_count, waves);
     prof_collect(prof, KSTAP_K_MGRAM);
     prof_begin(prof, KSTAP_K_MGRAM, s);
-    kstap::k_mgram<P, Q><<<gm, kstap::kWarpCells * 32, smg, s>>>(g, JL, Mw, Sw, Lw);
+    kstap::k_mgram<P, Q><<<gm, 64, smg, s>>>(g, JL, Mw, Sw, Lw);
     prof_end(prof, KSTAP_K_MGRAM, s);
     KSTAP_CUDA(ctx, cudaGetLastError());
     const size_t smf = smem_flipt(g);

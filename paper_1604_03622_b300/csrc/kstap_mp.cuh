@@ -2,8 +2,8 @@
 // rank-K spatial factor).  With p = 6 the p^2 x p^2 Gram M = R R^H has 666
 // complex entries, too many for one thread's registers: k_mgram forms M and
 // the block sums of S(i, k) from the exact lag store the moments pass wrote,
-// a warp per cell, and k_flipflop_t runs Alg. 2 with a thread per cell,
-// streaming M from the per-cell arrays.
+// a warp per strip of cells with sliding windows, and k_flipflop_t runs
+// Alg. 2 with a thread per cell, streaming M from the per-cell arrays.
 // The B / U_B pass (k_bfit) and the projection (k_detect) are the
 // single-pass kernels instantiated for more channels.  k_change forms the
 // per-pass maxima of the statistic and their difference (the noncoherent
@@ -14,7 +14,6 @@
 
 namespace kstap {
 
-constexpr int kWarpCells = 8;     // cells per CTA (one warp each) in k_mgram
 constexpr int kFlipThreads = 64;  // cells per CTA (one thread each) in k_flipflop_t
 
 // Row J of the Hermitian upper-triangle index: the J with
@@ -25,159 +24,206 @@ __device__ __forceinline__ void tri_rowcol(int n, int e, int& J, int& K) {
   K = J + (e - tri_idx(n, J, J));
 }
 
-// CTA = one cell row x kWarpCells cells, a warp per cell.  Per lag
-// g = Q-1 .. 0 the tile's lag sums (hi parts of the float-float store) are
-// staged as [position][J]; M = sum_g sum_j l_g(c + j) l_g(c + j)^H is
-// accumulated in P x P blocks, lane b < P(P+1)/2 owning block (I, K), I <= K,
-// of the PP x PP Gram (rows J = P I + a, columns P K + b): per position it
-// loads 2P entries of l and does P^2 complex multiply-adds.  The remaining
-// lanes accumulate the block sums s.  Before lag 0 the negative lags are
-// folded in (M += conj(Pi M Pi^T), s += conj(Pi s), Pi swapping the channel
-// pair (i, k) -> (k, i)), as in the single-pass moments kernel.
+// M = R R^H and the block sums of S(i, k) from the lag store, a CTA of two
+// warps per strip of kStrip consecutive cells of one row.  With l_g(u) the
+// PP-vector of lag-g sums at position u (hi parts of the float-float store),
+//   M(c) = F(X(c)),  X(c) = sum_g w_g sum_{u = c}^{c+Q-1-g} l_g(u) l_g(u)^H,
+// w_0 = 1/2, w_g = 1 otherwise, and F(X) = X + conj(Pi X Pi^T) (Pi swaps the
+// channel pair (i, k) -> (k, i); the negative lags are the Pi-conjugates of
+// the positive ones, and the lag-0 term is its own, hence the half weight).
+// Neighbouring cells share all but two positions per lag, so the CTA forms
+// X of its strip's first cell directly and then slides the windows:
+//   X(c+1) = X(c) + sum_g w_g (l_g(c+Q-g) l_g(c+Q-g)^H - l_g(c) l_g(c)^H),
+// 2Q outer products per cell instead of sum_g (Q - g) (restarting every
+// kStrip cells bounds the rounding growth of the running sums).  Lane
+// b < P(P+1)/2 of warp h holds rows P I + a, a in [hP/2, (h+1)P/2), of the
+// P x P block (I, K), I <= K, of X (columns P K + b); lanes above that in
+// warp 0 hold the block sums.  The current windows sit in a shared-memory
+// ring per lag (Q - g + 1 slots: the position that enters at a step lands in
+// the slot after the window), read by both warps; the next step's entering
+// positions are loaded into registers while the warps compute.
+constexpr int kStrip = 32;   // cells per CTA tile of k_mgram
+
+template <int Q>
+__host__ __device__ constexpr int ring_off(int g) {   // first ring slot of lag g
+  return g * (Q + 1) - (g * (g - 1)) / 2;
+}
+
 template <int P, int Q>
-__global__ void __launch_bounds__(kWarpCells * 32, 2)
+__global__ void __launch_bounds__(64)
 k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
         const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
-  constexpr int NE = PP * (PP + 1) / 2;
   constexpr int NBP = P * (P + 1) / 2;   // blocks of M on and above the diagonal
-  static_assert(NBP < 32 && P % 2 == 0, "a block per lane, 16-byte block rows");
-  constexpr int NSL = 32 - NBP;          // lanes for the block sums
+  constexpr int HR = P / 2;              // block rows per warp
+  static_assert(NBP < 32 && P % 2 == 0 && HR % 1 == 0, "a half block per lane");
+  constexpr int NSL = 32 - NBP;          // lanes of warp 0 for the block sums
   constexpr int SPL = (PP + NSL - 1) / NSL;
-  constexpr int TCm = kWarpCells;
-  constexpr int NUmax = TCm + Q - 1;
+  constexpr int NSLOT = ring_off<Q>(Q);  // ring slots of all lags
+  constexpr int NEW = Q * PP;            // entries of one step's entering positions
+  constexpr int NPL = (NEW + 63) / 64;   // of them per thread
+  constexpr int NX = kStrip + Q;         // offsets u - c0 that occur
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* Ls = reinterpret_cast<float2*>(smem);                 // [NUmax][PP]
-  float2* Ft = Ls + NUmax * PP;                                 // [warps][PP][PP] fold scratch
-  float2* Fs = Ft + kWarpCells * PP * PP;                       // [warps][PP]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* ring = reinterpret_cast<float2*>(smem);   // [NSLOT][PP]
+  float2* ft = ring + NSLOT * PP;                   // [PP][PP] fold scratch
+  float2* fs = ft + PP * PP;                        // [PP]
+  __shared__ unsigned char slot_tab[Q][NX];         // (u - c0) mod (Q - g + 1)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < Q * NX; e += 64) slot_tab[e / NX][e % NX] = (unsigned char)((e % NX) % (Q - e / NX + 1));
+  __syncthreads();
   const bool mlane = lane < NBP;
+  const bool slane = warp == 0 && !mlane;
+  const int a0 = warp * HR;
   int bI = 0, bK = 0;
   if (mlane) tri_rowcol(P, lane, bI, bK);
+  const size_t ncell = (size_t)JL.NC;
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindMgram]; tile += gridDim.x) {
     int lt;
     const Job& JB = job_of(JL, kKindMgram, tile, lt);
     const Geom g = with_job(g0, JB);
     const float4* __restrict__ Lw = Lw0 + JB.lag0;
-    const int ntx = (g.W + TCm - 1) / TCm;
-    const int r = lt / ntx, c0 = (lt % ntx) * TCm;
-    const int cl = warp;
-    const bool live = c0 + cl < g.W;
+    const int ntx = (g.W + kStrip - 1) / kStrip;
+    const int r = lt / ntx, c0 = (lt % ntx) * kStrip;
+    const int ncl = min(kStrip, g.W - c0);
     const int WL = g.W + Q - 1;
-    float2 acc[P][P], sacc[SPL];
+    const float4* __restrict__ rowL = Lw + (size_t)r * Q * PP * WL;
+    // lag-g sum J at position u: rowL[(g PP + J) WL + u]; its ring slot is
+    // ring_off(g) + (u - c0) mod (Q - g + 1)
+    auto slot = [&](int lg, int u) { return ring_off<Q>(lg) + slot_tab[lg][u - c0]; };
+    // the first cell's windows: positions c0 .. c0 + Q - 1 - g of every lag
+    for (int e = tid; e < NSLOT * PP; e += 64) {
+      const int sl = e / PP, J = e - sl * PP;
+      int lg = 0;
+      while (lg + 1 < Q && ring_off<Q>(lg + 1) <= sl) ++lg;
+      const int k = sl - ring_off<Q>(lg);   // position c0 + k
+      if (k < Q - lg) {
+        const float4 v = __ldg(rowL + ((size_t)lg * PP + J) * WL + c0 + k);
+        ring[sl * PP + J] = make_float2(v.x, v.z);
+      }
+    }
+    __syncthreads();
+    float2 acc[HR][P], sacc[SPL];
 #pragma unroll
-    for (int a = 0; a < P; ++a)
+    for (int a = 0; a < HR; ++a)
 #pragma unroll
       for (int b = 0; b < P; ++b) acc[a][b] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < SPL; ++t) sacc[t] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int lagg = Q - 1; lagg >= 0; --lagg) {
-      const int NU = TCm + Q - 1 - lagg;
-      const float4* src = Lw + ((size_t)r * Q + lagg) * PP * WL;
-      for (int idx = threadIdx.x; idx < PP * NU; idx += blockDim.x) {
-        const int u = idx / PP, J = idx - u * PP;
-        const float4 v = (c0 + u < WL) ? __ldg(src + (size_t)J * WL + c0 + u)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-        Ls[u * PP + J] = make_float2(v.x, v.z);
-      }
-      __syncthreads();
-      if (lagg == 0) {
-        // fold the negative lags into the sums over g > 0.  The whole
-        // Hermitian W goes to shared memory; Pi maps entry (a, b) of block
-        // (I, K) to entry (I, K) of block (a, b), so each lane reads its
-        // partners at fixed offsets from one base.
-        float2* ft = Ft + warp * PP * PP;
-        float2* fs = Fs + warp * PP;
-        if (mlane) {
-#pragma unroll
-          for (int a = 0; a < P; ++a)
-#pragma unroll
-            for (int b = 0; b < P; ++b) {
-              const int J = P * bI + a, K = P * bK + b;
-              if (bI == bK && a > b) continue;
-              ft[J * PP + K] = acc[a][b];
-              ft[K * PP + J] = cconj(acc[a][b]);
-            }
-        } else {
-#pragma unroll
-          for (int t = 0; t < SPL; ++t) {
-            const int J = (lane - NBP) + NSL * t;
-            if (J < PP) fs[J] = sacc[t];
-          }
-        }
-        __syncwarp();
-        if (mlane) {
-          const float2* fp = ft + bI * PP + bK;   // W[P a + I][P b + K] = fp[a P PP + b P]
-#pragma unroll
-          for (int a = 0; a < P; ++a)
-#pragma unroll
-            for (int b = 0; b < P; ++b) {
-              if (bI == bK && a > b) continue;
-              acc[a][b] = cadd(acc[a][b], cconj(fp[a * P * PP + b * P]));
-            }
-        } else {
-#pragma unroll
-          for (int t = 0; t < SPL; ++t) {
-            const int J = (lane - NBP) + NSL * t;
-            if (J < PP) sacc[t] = cadd(sacc[t], cconj(fs[(J % P) * P + J / P]));
-          }
-        }
-        __syncwarp();
-      }
-      if (live) {
-#pragma unroll 1
-        for (int j = 0; j < Q - lagg; ++j) {
-          const float2* l = Ls + (cl + j) * PP;
-          if (mlane) {
-            float2 x[P], y[P];
-            const float4* lx = reinterpret_cast<const float4*>(l + P * bI);
-            const float4* ly = reinterpret_cast<const float4*>(l + P * bK);
-#pragma unroll
-            for (int h = 0; h < P / 2; ++h) {
-              const float4 v = lx[h], w = ly[h];
-              x[2 * h] = make_float2(v.x, v.y);
-              x[2 * h + 1] = make_float2(v.z, v.w);
-              y[2 * h] = make_float2(w.x, w.y);
-              y[2 * h + 1] = make_float2(w.z, w.w);
-            }
-#pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-              for (int b = 0; b < P; ++b) {   // l[J] conj(l[K])
-                acc[a][b].x += x[a].x * y[b].x + x[a].y * y[b].y;
-                acc[a][b].y += x[a].y * y[b].x - x[a].x * y[b].y;
-              }
-          } else {
-#pragma unroll
-            for (int t = 0; t < SPL; ++t) {
-              const int J = (lane - NBP) + NSL * t;
-              if (J < PP) sacc[t] = cadd(sacc[t], l[J]);
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-    if (live) {
-      const size_t ncell = (size_t)JL.NC;
-      const size_t cell = (size_t)JB.cell0 + (size_t)r * g.W + (c0 + cl);
+    // w l l^H into the thread's half block, or w l into the block sums
+    // (w = +-1 folds into the multiply-adds; lag 0 passes its half weight)
+    auto outer = [&](const float2* l, float w) {
       if (mlane) {
+        float2 x[HR], y[P];
+        const float2* lx = l + P * bI + a0;
+        const float4* ly = reinterpret_cast<const float4*>(l + P * bK);
 #pragma unroll
-        for (int a = 0; a < P; ++a)
+        for (int a = 0; a < HR; ++a) x[a] = w == 1.f ? lx[a] : make_float2(w * lx[a].x, w * lx[a].y);
 #pragma unroll
-          for (int b = 0; b < P; ++b) {
-            const int J = P * bI + a, K = P * bK + b;
-            if (J <= K) Mw[(size_t)tri_idx(PP, J, K) * ncell + cell] = acc[a][b];
+        for (int h = 0; h < P / 2; ++h) {
+          const float4 u = ly[h];
+          y[2 * h] = make_float2(u.x, u.y);
+          y[2 * h + 1] = make_float2(u.z, u.w);
+        }
+#pragma unroll
+        for (int a = 0; a < HR; ++a)
+#pragma unroll
+          for (int b = 0; b < P; ++b) {   // x[a] conj(y[b])
+            acc[a][b].x += x[a].x * y[b].x + x[a].y * y[b].y;
+            acc[a][b].y += x[a].y * y[b].x - x[a].x * y[b].y;
           }
-      } else {
+      } else if (slane) {
 #pragma unroll
         for (int t = 0; t < SPL; ++t) {
           const int J = (lane - NBP) + NSL * t;
-          if (J < PP) Sw[(size_t)J * ncell + cell] = sacc[t];
+          if (J < PP) sacc[t] = make_float2(sacc[t].x + w * l[J].x, sacc[t].y + w * l[J].y);
+        }
+      }
+    };
+#pragma unroll 1
+    for (int lg = 0; lg < Q; ++lg) {
+      const float w = lg == 0 ? 0.5f : 1.f;
+#pragma unroll 1
+      for (int k = 0; k < Q - lg; ++k) outer(ring + (ring_off<Q>(lg) + k) * PP, w);
+    }
+    float2 nv[NPL];
+    auto load_new = [&](int c) {   // positions c + Q - 1 - g entering the windows of cell c
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        const int e = tid + 64 * t;
+        nv[t] = make_float2(0.f, 0.f);
+        if (e < NEW) {
+          const int lg = e / PP, J = e - lg * PP;
+          const float4 v = __ldg(rowL + ((size_t)lg * PP + J) * WL + c + Q - 1 - lg);
+          nv[t] = make_float2(v.x, v.z);
+        }
+      }
+    };
+    if (ncl > 1) load_new(c0 + 1);
+#pragma unroll 1
+    for (int cl = 0; cl < ncl; ++cl) {
+      const int c = c0 + cl;
+      if (cl > 0) {
+        // slide every window from cell c - 1 to c: the positions c + Q - 1 - g
+        // enter (from registers into their ring slots), c - 1 leaves
+#pragma unroll
+        for (int t = 0; t < NPL; ++t) {
+          const int e = tid + 64 * t;
+          if (e < NEW) {
+            const int lg = e / PP, J = e - lg * PP;
+            ring[slot(lg, c + Q - 1 - lg) * PP + J] = nv[t];
+          }
+        }
+        __syncthreads();
+        if (cl + 1 < ncl) load_new(c + 1);
+#pragma unroll 1
+        for (int lg = 0; lg < Q; ++lg) {
+          const float w = lg == 0 ? 0.5f : 1.f;
+          outer(ring + slot(lg, c + Q - 1 - lg) * PP, w);
+          outer(ring + slot(lg, c - 1) * PP, -w);
+        }
+      }
+      // M(c) = X + conj(Pi X Pi^T): the whole Hermitian X through shared
+      // memory; Pi maps entry (a, b) of block (I, K) to entry (I, K) of
+      // block (a, b), so each thread reads its partners at fixed offsets
+      if (mlane) {
+#pragma unroll
+        for (int a = 0; a < HR; ++a)
+#pragma unroll
+          for (int b = 0; b < P; ++b) {
+            if (bI == bK && a0 + a > b) continue;
+            const int J = P * bI + a0 + a, K = P * bK + b;
+            ft[J * PP + K] = acc[a][b];
+            ft[K * PP + J] = cconj(acc[a][b]);
+          }
+      } else if (slane) {
+#pragma unroll
+        for (int t = 0; t < SPL; ++t) {
+          const int J = (lane - NBP) + NSL * t;
+          if (J < PP) fs[J] = sacc[t];
+        }
+      }
+      __syncthreads();
+      const size_t cell = (size_t)JB.cell0 + (size_t)r * g.W + c;
+      if (mlane) {
+        const float2* fp = ft + bI * PP + bK;   // X[P a + I][P b + K] = fp[a P PP + b P]
+#pragma unroll
+        for (int a = 0; a < HR; ++a)
+#pragma unroll
+          for (int b = 0; b < P; ++b) {
+            if (bI == bK && a0 + a > b) continue;
+            const int J = P * bI + a0 + a, K = P * bK + b;
+            Mw[(size_t)tri_idx(PP, J, K) * ncell + cell] =
+                cadd(acc[a][b], cconj(fp[(a0 + a) * P * PP + b * P]));
+          }
+      } else if (slane) {
+#pragma unroll
+        for (int t = 0; t < SPL; ++t) {
+          const int J = (lane - NBP) + NSL * t;
+          if (J < PP) Sw[(size_t)J * ncell + cell] = cadd(sacc[t], cconj(fs[(J % P) * P + J / P]));
         }
       }
     }
+    __syncthreads();   // the next tile refills the ring
   }
 }
 
