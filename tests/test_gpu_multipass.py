@@ -210,3 +210,26 @@ def test_stacked_pass_batch_strips_and_serving():
     got = ks.run(Y, T_all=True)["T_all"].cpu().numpy()
     ks.close()
     assert t_err(got, ref.astype(np.float64)).max() <= 1e-4
+
+
+def test_change_map_three_passes_and_flagged_cells():
+    """kstap_change_map for K = 3 passes on a synthetic T_all: per-pass maxima
+    bit-exact against numpy, change = last minus first pass, and a flagged
+    cell (T_all NaN) stays NaN."""
+    import torch
+    import paper_1604_03622_b300 as K
+    rng = np.random.default_rng(31)
+    ncell, V, KP = 1000, 7, 3
+    T = rng.exponential(size=(ncell, KP * V)).astype(np.float32)
+    T[17] = np.nan
+    Tk, ch = K.kstap_change_map(torch.from_numpy(T).cuda(), V, KP)
+    torch.cuda.synchronize()
+    Tk, ch = Tk.cpu().numpy(), ch.cpu().numpy()
+    ok = np.ones(ncell, bool)
+    ok[17] = False
+    per = T.reshape(ncell, KP, V).max(axis=2).T
+    assert np.array_equal(Tk[:, ok], per[:, ok])
+    assert np.array_equal(ch[ok], per[-1, ok] - per[0, ok])
+    assert np.isnan(Tk[:, 17]).all() and np.isnan(ch[17])
+    with pytest.raises(ValueError):
+        K.kstap_change_map(torch.from_numpy(T).cuda(), V + 1, KP)
