@@ -233,6 +233,15 @@ TRAFFIC = {
 }
 
 
+def measured_peak(key: str):
+    """A figure of MEASURED_PEAKS.json (measured on this machine), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_traffic(workload: str, precision: str, kernel: str):
     import hashlib
     t = TRAFFIC.get((workload, precision, kernel))
@@ -355,6 +364,20 @@ def precision_leg(dev, steps: int, warmup: int):
         out[prec] = dict(cells_per_s=wl.cells * len(ms) / (sum(ms) / 1e3),
                          ms_per_frame=sum(ms) / len(ms), p99_ms=sorted(ms)[-1],
                          kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()})
+        if prec != "fp32":
+            # tensor-pipe roofline of the bank contraction: per cell the GEMM
+            # rows are 2 (p + r_b) real operand rows (Re|Im, Im|-Re), K = 2q,
+            # V velocities, three 16-bit products (hi hi, hi lo, lo hi)
+            det_ms = kt["detect"][0] / max(kt["detect"][1], 1)
+            flops = 3 * 2 * wl.V * 2 * (wl.p + wl.r_b) * 2 * wl.q * wl.cells
+            peak = measured_peak("bf16_tflops")
+            achieved = flops / (det_ms / 1e3) / 1e12
+            out[prec]["detect_roofline"] = dict(
+                bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=achieved / peak if peak else None, kernel="detect",
+                note="MMA flops of the bank contraction over the whole detect kernel time "
+                     "(the projection and epilogue on the CUDA cores dominate it); peak = "
+                     "measured dense bf16 burst (fp16 has the same dense rate)")
     del Y, flush
     torch.cuda.empty_cache()
     return out
@@ -498,13 +521,15 @@ def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
 
 
 # ----------------------------------------------------------------- serving ---
-def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
+def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
+                batched_cfg=(16, 4, 1 << 20), extra_cfgs=()):
     """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
     V = 64) at 0.8 x the measured plain capacity, through kstap_submit /
     kstap_poll with a 120 GB HBM budget (60 GB per q class).  plain: one frame
     at a time (batch 1, one stream, FP32 bank); batched: continuous batching
-    (batch <= 16, 4 streams, bank on the tensor cores).  Latency = completion
-    - arrival."""
+    (batch <= 16 frames and <= 1 M cells, 4 streams, bank on the tensor cores).
+    Latency = completion - arrival.  extra_cfgs: more (max_batch, streams,
+    batch cells) configurations of the batched arm, reported under "extra"."""
     import threading
     import torch
     import gen
@@ -534,7 +559,7 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
     rate = 0.8 / float(np.mean(per_frame_s))
     t_arr, pick = gen.poisson_arrivals(n_requests, rate, len(pool))
 
-    def run(max_batch, max_inflight, prec):
+    def run(max_batch, max_inflight, prec, cap=None):
         ctxs = {}
         for q in qs:
             i0 = [i for i, w in enumerate(pool) if w.q == q][0]
@@ -542,6 +567,8 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
                                      device=str(dev), hbm_budget_bytes=budget // len(qs),
                                      precision=prec)
             K.kstap_serve_config(ks.ctx, max_batch, max_inflight)
+            if cap is not None:
+                K.kstap_serve_batch_cells(ks.ctx, cap)
             ctxs[q] = ks
         tickets = [None] * n_requests
         t0 = time.perf_counter()
@@ -576,15 +603,16 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3"):
         return dict(cells_per_s=cells / t_end, p50_ms=lat[len(lat) // 2],
                     p99_ms=lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                     mean_ms=float(np.mean(lat)), wall_s=t_end, max_batch=max_batch,
-                    streams=max_inflight, precision=prec)
+                    streams=max_inflight, precision=prec, batch_cells=cap)
 
     plain = run(1, 1, "fp32")
-    batched = run(16, 4, precision)
+    batched = run(batched_cfg[0], batched_cfg[1], precision, batched_cfg[2])
+    extra = [run(mb, mi, precision, cap) for (mb, mi, cap) in extra_cfgs]
     return dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
                 q=qs, r_b=3, V=64, budget_gb=120, arrival_rate_hz=rate,
                 plain_capacity_frames_per_s=1.0 / float(np.mean(per_frame_s)),
                 mean_cells_per_frame=float(np.mean([pool[int(i)].cells for i in pick])),
-                plain=plain, batched=batched)
+                plain=plain, batched=batched, **({"extra": extra} if extra else {}))
 
 
 # ------------------------------------------------------------------ main ----
@@ -642,6 +670,7 @@ def main():
     kt = K.kstap_kernel_times(ks.ctx)
     K.kstap_set_profiling(ks.ctx, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    iters_mean = float(ks.buffers(wl.H_in, wl.W_in)["iters"].float().mean().item())
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     value = job_value(ncell, args.steps, ws, total_ms)
 
@@ -728,6 +757,7 @@ def main():
                     p=wl.p, q=wl.q,
                     r_a=wl.r_a, r_b=wl.r_b, n=wl.n, V=wl.V, cnr_db=wl.cnr_db,
                     l2="256 MiB flush between timed steps, outside the events",
+                    flipflop_iters_mean=iters_mean,
                     parallelism=f"replicas x{ws}"),
         latency_ms=dict(p50=lat[len(lat) // 2], p99=lat[min(len(lat) - 1,
                                                             math.ceil(0.99 * len(lat)) - 1)]),

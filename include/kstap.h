@@ -279,6 +279,13 @@ typedef struct {
 /* Serving limits: frames per batch (1..1024, default 16) and batches in
  * flight (1..16, default 4).  Call before the first kstap_submit. */
 kstap_status kstap_serve_config(kstap_ctx* ctx, int max_batch, int max_inflight);
+/* Work cap of one served batch in cells (H * W summed over its frames and
+ * strips; a single frame or strip above the cap still forms a batch of its
+ * own).  Every frame of a batch completes when the batch does, so the cap
+ * bounds how long a small frame waits for the large ones batched with it.
+ * cells <= 0 removes the cap; the default is 1 << 20.  Call before the first
+ * kstap_submit. */
+kstap_status kstap_serve_batch_cells(kstap_ctx* ctx, long long cells);
 /* flags: KSTAP_FRAME_ON_HOST when Y is in host memory (pinned for overlap). */
 kstap_status kstap_submit(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in, int flags,
                           uint64_t* ticket);

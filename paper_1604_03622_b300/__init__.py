@@ -25,7 +25,7 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
             "kstap_release", "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
-            "kstap_change_map"]
+            "kstap_change_map", "kstap_serve_batch_cells"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect", "mgram"]
 
 
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(KstapTuning)]
         L.kstap_set_tuning.argtypes = [P, ctypes.POINTER(KstapTuning)]
         L.kstap_serve_config.argtypes = [P, I, I]
+        L.kstap_serve_batch_cells.argtypes = [P, ctypes.c_longlong]
         L.kstap_submit.argtypes = [P, P, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
         L.kstap_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KstapResult), I]
         L.kstap_release.argtypes = [P, ctypes.c_uint64]
@@ -119,7 +120,7 @@ def lib() -> ctypes.CDLL:
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
                      "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
                      "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
-                     "kstap_change_map"):
+                     "kstap_change_map", "kstap_serve_batch_cells"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -296,6 +297,11 @@ def kstap_set_tuning(ctx: int, waves: int, tc: int = 0) -> None:
 
 def kstap_serve_config(ctx: int, max_batch: int, max_inflight: int) -> None:
     _check(lib().kstap_serve_config(ctx, max_batch, max_inflight), ctx)
+
+
+def kstap_serve_batch_cells(ctx: int, cells: int) -> None:
+    """Work cap of one served batch in cells (<= 0: none; default 1 << 20)."""
+    _check(lib().kstap_serve_batch_cells(ctx, int(cells)), ctx)
 
 
 def kstap_submit(ctx: int, Y, H_in: int, W_in: int, on_host: bool = False) -> int:

@@ -1230,6 +1230,7 @@ struct Server {
   int inflight = 0;
   int max_batch = 16;
   int max_inflight = 4;
+  long long max_batch_cells = 1LL << 20;   // <= 0: no cap
   uint64_t next_ticket = 1;
   std::vector<cudaStream_t> streams;
   int rr = 0;
@@ -1370,6 +1371,11 @@ void worker_loop(Server* s) {
   auto part_bytes = [&](const std::pair<uint64_t, int>& it) {
     return s->reqs[it.first].parts[it.second].scratch_bytes;
   };
+  const kstap_params& p = s->ctx->prm;
+  auto part_cells = [&](const std::pair<uint64_t, int>& it) {
+    const Frame& f = s->reqs[it.first].parts[it.second].fr;
+    return (long long)(f.H_in - 2 * p.ring_r) * (f.W_in - 2 * p.ring_a - p.q + 1);
+  };
   while (true) {
     s->cv.wait(lock, [&] {
       if (s->stop) return true;
@@ -1379,11 +1385,15 @@ void worker_loop(Server* s) {
     });
     if (s->stop) break;
     std::vector<std::pair<uint64_t, int>> batch;
+    long long cells = 0;
     while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
       const auto it = s->pending.front();
       const size_t need = part_bytes(it);
       if (s->ctx->budget && s->used + need > s->ctx->budget && !(batch.empty() && s->inflight == 0))
         break;
+      const long long nc = part_cells(it);
+      if (!batch.empty() && s->max_batch_cells > 0 && cells + nc > s->max_batch_cells) break;
+      cells += nc;
       s->used += need;
       Server::Req& r = s->reqs[it.first];
       r.parts[it.second].state = 1;
@@ -1443,6 +1453,19 @@ void server_shutdown(kstap_ctx* ctx) {
 }
 
 extern "C" {
+
+kstap_status kstap_serve_batch_cells(kstap_ctx* ctx, long long cells) {
+  if (!ctx) return KSTAP_EINVAL;
+  Server* s = get_server(ctx);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->next_ticket == 1) {   // nothing submitted yet
+      s->max_batch_cells = cells;
+      return KSTAP_OK;
+    }
+  }
+  return fail(ctx, KSTAP_EINVAL, "configure serving before the first submit");
+}
 
 kstap_status kstap_serve_config(kstap_ctx* ctx, int max_batch, int max_inflight) {
   if (!ctx) return KSTAP_EINVAL;
