@@ -328,11 +328,13 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
 
 
 # --------------------------------------------------------- q = 32 frame ---
-def precision_leg(dev, steps: int, warmup: int):
+def precision_leg(dev, steps: int, warmup: int, err_cells: int = 256, cpu: bool = True):
     """The 2048 x 2048-cell q = 32 frame (p = 3, r_b = 4, n = 192, V = 128,
     40 dB CNR): plain path, per-step CUDA events with an L2 flush between
-    steps, once with the FP32 bank and once with the FP16X3 tensor-core bank;
-    per-kernel times from the library's events."""
+    steps, with the FP32 bank and with the FP16X3 and BF16X3 tensor-core banks;
+    per-kernel times from the library's events; the error of the statistic
+    against the FP64 oracle on `err_cells` seeded cells (all V velocities):
+    max |T - T_ref| / max(T_ref, sigma^2)."""
     import torch
     import gen
     import paper_1604_03622_b300 as K
@@ -343,7 +345,13 @@ def precision_leg(dev, steps: int, warmup: int):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = dict(workload=wl.name, cells_per_frame=wl.cells, q=wl.q, r_b=wl.r_b, n=wl.n, V=wl.V)
-    for prec in ("fp32", "fp16x3"):
+    ref = None
+    if cpu and err_cells > 0:
+        import oracle
+        cells = gen.random_cells(wl, err_cells, seed=77)
+        ref = oracle.run_workload(f, cells=cells, want_proj=False)
+        out["error_sample"] = f"{len(cells)} seeded random cells x {wl.V} velocities (FP64 oracle)"
+    for prec in ("fp32", "fp16x3", "bf16x3"):
         ks = KStap.from_workload(wl, f.bank_a, f.bank_b, device=str(dev), stream=stream,
                                  precision=prec)
         for _ in range(warmup):
@@ -360,9 +368,16 @@ def precision_leg(dev, steps: int, warmup: int):
             b.synchronize()
             ms.append(a.elapsed_time(b))
         kt = K.kstap_kernel_times(ks.ctx)
+        K.kstap_set_profiling(ks.ctx, False)
+        err = None
+        if ref is not None:
+            T = ks.run(Y, T_all=True)["T_all"][torch.from_numpy(ref["cells"]).to(dev)]
+            T = T.double().cpu().numpy()
+            err = float((np.abs(T - ref["T_all"]) / np.maximum(ref["T_all"], wl.sigma2)).max())
         ks.close()
         out[prec] = dict(cells_per_s=wl.cells * len(ms) / (sum(ms) / 1e3),
                          ms_per_frame=sum(ms) / len(ms), p99_ms=sorted(ms)[-1],
+                         max_rel_err_T=err,
                          kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()})
         if prec != "fp32":
             # tensor-pipe roofline of the bank contraction: per cell the GEMM
@@ -727,7 +742,8 @@ def main():
 
     serving = None if args.no_serving else serving_leg(dev, args.serve_requests)
 
-    precision = None if args.no_precision_leg else precision_leg(dev, 3, 3)
+    precision = None if args.no_precision_leg else precision_leg(
+        dev, 3, 3, cpu=not args.no_cpu_baseline)
 
     robustness = None if args.no_robustness else robustness_leg(dev)
 
