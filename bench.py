@@ -689,25 +689,50 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     value = job_value(ncell, args.steps, ws, total_ms)
 
-    # ---- e2e: pinned host frame in, Tmax / vidx / map out, through the C ABI
+    # ---- e2e: pinned host frame in, Tmax / vidx / map out, through the C ABI.
+    # Every step copies its frame host -> device and its results back inside
+    # the timed region; the copy of frame s + 1 runs on a second stream while
+    # frame s is processed (two device frame buffers), as a streaming user of
+    # the library would run it.  The timed region spans the first copy to the
+    # last result read.
     Yh = [torch.from_numpy(f.Y).pin_memory() for f in frames]
-    Yd = torch.empty_like(Ys[0])
+    Ydb = [torch.empty_like(Ys[0]) for _ in range(2)]
     outh = dict(Tmax=torch.empty(ncell, dtype=torch.float32).pin_memory(),
                 vidx=torch.empty(ncell, dtype=torch.int32).pin_memory(),
                 map=torch.empty(ncell, dtype=torch.uint8).pin_memory())
+    cstream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+
+    def copy_in(k):
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(freed[k % 2])      # buffer k % 2 no longer read
+            Ydb[k % 2].copy_(Yh[k % 2], non_blocking=True)
+            copied[k % 2].record(cstream)
+
+    def e2e_steps(n, timed):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        cstream.wait_event(ev0)
+        copy_in(0)
+        for k in range(n):
+            if k + 1 < n:
+                copy_in(k + 1)
+            stream.wait_event(copied[k % 2])
+            flush.fill_(k & 0xff)
+            o = ks.run(Ydb[k % 2])
+            freed[k % 2].record(stream)
+            for key in outh:
+                outh[key].copy_(o[key], non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
     e2e_ms = []
-    for s in range(0 if args.no_e2e else args.warmup + args.steps):
-        flush.fill_(s & 0xff)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        Yd.copy_(Yh[s % 2], non_blocking=True)
-        o = ks.run(Yd)
-        for k in outh:
-            outh[k].copy_(o[k], non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if s >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
+    if not args.no_e2e:
+        e2e_steps(args.warmup, False)
+        e2e_ms = [e2e_steps(args.steps, True)]
     e2e_total = max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), ws, dev)
     e2e_value = job_value(ncell, args.steps, ws, e2e_total)
     h2d = frames[0].Y.nbytes
@@ -779,7 +804,9 @@ def main():
                                                             math.ceil(0.99 * len(lat)) - 1)]),
         e2e=None if args.no_e2e else dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d,
                                           d2h_bytes_per_step=d2h,
-                                          ms_per_step=e2e_total / args.steps),
+                                          ms_per_step=e2e_total / args.steps,
+                                          overlap="the copy of frame s+1 runs on a second "
+                                                  "stream during frame s"),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
         batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing,
