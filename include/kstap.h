@@ -308,8 +308,9 @@ kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket);
  * Scratch (frame scale, per-cell moments and flip-flop factors, 504 B per
  * cell) lives in one statically allocated device array of about 16.5 MB that
  * every GPU which loads the library holds until the process exits.  Frames
- * with more than 32768 cells (H * W) are rejected with KSTAP_EINVAL and a
- * message from kstap_last_error(NULL); other errors are reported the same way.
+ * with more than 32768 cells (H * W), and parameters with p != 3, are
+ * rejected with KSTAP_EINVAL and a message from kstap_last_error(NULL); other
+ * errors are reported the same way.
  *
  * The first call on each device looks up that device's address of the array
  * (with that device current); make that first call before any stream
