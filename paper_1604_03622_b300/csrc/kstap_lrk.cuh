@@ -94,22 +94,27 @@ __global__ void k_lrk_tmat(const double2* __restrict__ G, int n, int p, double2*
 
 // Cyclic Jacobi on a Hermitian p x p matrix (FP64, row-major in `A`); on
 // return w holds the eigenvalues in decreasing order and the columns of U
-// (row-major) the eigenvectors.
+// (row-major) the eigenvectors.  Off-diagonal entries at or below the
+// matrix's rounding level (1e-16 of sum |A_ii|) are set to zero instead of
+// rotated: without that floor the entries between eigenvalues near zero
+// (a rank-one A has p - 1 of them) keep the sweeps going to the cap.
 __device__ void lrk_jacobi(double2* A, int p, double* w, double2* U) {
   for (int i = 0; i < p; ++i)
     for (int j = 0; j < p; ++j) U[i * p + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, diag = 0.0;
+    double off = 0.0, diag = 0.0, tr = 0.0;
     for (int i = 0; i < p; ++i) {
       diag += A[i * p + i].x * A[i * p + i].x;
+      tr += fabs(A[i * p + i].x);
       for (int j = i + 1; j < p; ++j) off += zabs2(A[i * p + j]);
     }
     if (off <= 1e-30 * diag || off == 0.0) break;
+    const double floor_ab = 1e-16 * tr;
     for (int a = 0; a < p - 1; ++a)
       for (int b = a + 1; b < p; ++b) {
         const double2 apq = A[a * p + b];
         const double ab = hypot(apq.x, apq.y);   // no squaring: no underflow for tiny entries
-        if (!(ab > 1e-20 * (fabs(A[a * p + a].x) + fabs(A[b * p + b].x)))) {
+        if (!(ab > fmax(1e-20 * (fabs(A[a * p + a].x) + fabs(A[b * p + b].x)), floor_ab))) {
           A[a * p + b] = A[b * p + a] = make_double2(0.0, 0.0);
           continue;
         }
@@ -177,9 +182,10 @@ __global__ void k_lrk_iterate(const double2* __restrict__ Tm, const double2* __r
                               double eps, int max_iter, double2* __restrict__ A_fin,
                               double2* __restrict__ A_prev, double* __restrict__ info) {
   constexpr int PP = kLrkMaxP * kLrkMaxP;
-  __shared__ double2 a[PP], t[PP], Am[PP], U[PP];
+  __shared__ double2 a[PP], t[PP], Am[PP], U[PP], Ub[PP], Tt[PP];
   __shared__ double w[kLrkMaxP];
-  __shared__ int done;
+  __shared__ int done, ok;
+  __shared__ double sh_f, sh_an, sh_bn;
   const int lane = threadIdx.x, p2 = p * p, np = n * p;
   double Rn2 = 0.0;
   if (lane == 0) {
@@ -198,6 +204,8 @@ __global__ void k_lrk_iterate(const double2* __restrict__ Tm, const double2* __r
       }
     done = 0;
   }
+  for (int e = lane; e < p2; e += 32)   // eigenbasis of the previous iterate: I
+    Ub[e] = make_double2(e / p == e % p ? 1.0 : 0.0, 0.0);
   __syncwarp();
   double eta_prev = 1.0 / 0.0, an_prev = 0.0, eta = 0.0;
   int it = 0;
@@ -216,16 +224,63 @@ __global__ void k_lrk_iterate(const double2* __restrict__ Tm, const double2* __r
       }
       const double nn = (double)n * n;
       const double bn = (an > 0.0) ? ip / (nn * an * an) : 0.0;
-      if (!(an > 0.0) || !(bn > 0.0)) {
+      ok = (an > 0.0) && (bn > 0.0);
+      if (!ok) {
         done = 1;
       } else {
         const double f = 1.0 / (nn * an * bn);
+        sh_f = f;
+        sh_an = an;
+        sh_bn = bn;
         for (int i = 0; i < p; ++i)        // herm(vec^-1 a~), row-major
           for (int k = 0; k < p; ++k) {
             const double2 x = t[i + p * k], y = t[k + p * i];
             Am[i * p + k] = make_double2(0.5 * f * (x.x + y.x), 0.5 * f * (x.y - y.y));
           }
-        lrk_jacobi(Am, p, w, U);
+      }
+    }
+    __syncwarp();
+    if (!ok) break;
+    // EIG of A~ warm-started in the previous iterate's eigenbasis Ub: B =
+    // Ub^H A~ Ub is nearly diagonal, so the Jacobi below needs a sweep or two
+    // (the iterates change little from one step to the next); U = Ub W.
+    for (int e = lane; e < p2; e += 32) {   // Tt = A~ Ub
+      const int i = e / p, m = e % p;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < p; ++k) acc = zadd(acc, zmul(Am[i * p + k], Ub[k * p + m]));
+      Tt[e] = acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < p2; e += 32) {   // B = Ub^H Tt (into Am, now free)
+      const int m = e / p, k2 = e % p;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = 0; i < p; ++i) acc = zadd(acc, zmul(zconj(Ub[i * p + m]), Tt[i * p + k2]));
+      Am[e] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      for (int m = 0; m < p; ++m)           // Hermitian part, pairwise in place
+        for (int k2 = m; k2 < p; ++k2) {
+          const double2 x = Am[m * p + k2], y = Am[k2 * p + m];
+          const double2 h = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+          Am[m * p + k2] = h;
+          Am[k2 * p + m] = zconj(h);
+        }
+      lrk_jacobi(Am, p, w, U);
+    }
+    __syncwarp();
+    for (int e = lane; e < p2; e += 32) {   // U = Ub W
+      const int i = e / p, m = e % p;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < p; ++k) acc = zadd(acc, zmul(Ub[i * p + k], U[k * p + m]));
+      Tt[e] = acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < p2; e += 32) U[e] = Ub[e] = Tt[e];
+    __syncwarp();
+    if (lane == 0) {
+      {
+        const double f = sh_f, an = sh_an, bn = sh_bn;
         double anew = 0.0, re = 0.0;
         for (int i = 0; i < p; ++i)
           for (int k = 0; k < p; ++k) {
