@@ -49,3 +49,15 @@ def compare(gpu, ref, cells, tau, tol=TOL_T, check_all_T=True):
         bad = (gpu["vidx"][k] != ref["vidx"]) & ok
         assert not bad.any(), f"{bad.sum()} argmax mismatches"
     return rep
+
+
+def run_sampled(ks, Y, cells):
+    """One fit + detect of device frame Y through context `ks` (a KStap); the
+    statistic and the maps of the listed cells only, copied to the host (a
+    full-size frame's T_all and factors are gigabytes)."""
+    import torch
+    out = ks.run(Y, T_all=True)
+    idx = torch.from_numpy(np.asarray(cells, np.int64)).to(Y.device)
+    res = {k: out[k][idx].cpu().numpy() for k in ("T_all", "Tmax", "vidx", "map")}
+    torch.cuda.synchronize()
+    return res

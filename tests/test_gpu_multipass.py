@@ -233,3 +233,23 @@ def test_change_map_three_passes_and_flagged_cells():
     assert np.isnan(Tk[:, 17]).all() and np.isnan(ch[17])
     with pytest.raises(ValueError):
         K.kstap_change_map(torch.from_numpy(T).cuda(), V + 1, KP)
+
+
+def test_stacked_pass_full_size_frame_sampled():
+    """The two-pass 1024 x 1024 frame of the bench's stacked-pass leg, run
+    whole; all 2V velocities compared on every target cell and 512 random
+    cells."""
+    import torch
+    from gpu_common import run_sampled
+    from paper_1604_03622_b300.runner import KStap
+    f = _frame("frame1024", 1024, 1024)
+    wl = f.wl
+    tcells = [r * wl.W + c for _, r, c, _, _ in f.targets]
+    cells = np.unique(np.concatenate([tcells, gen.random_cells(wl, 512, seed=10)]).astype(np.int64))
+    ks = KStap(K_PASSES * wl.p, wl.q, 2, wl.r_b, wl.ring_r, wl.ring_a, wl.guard_r, wl.guard_a,
+               wl.tau, f.bank_a, f.bank_b)
+    gpu = run_sampled(ks, torch.from_numpy(f.Y).cuda(), cells)
+    ks.close()
+    ref = _oracle(f, 2, cells=cells)
+    rep = compare(gpu, ref, np.arange(len(cells)), wl.tau)
+    print(rep)

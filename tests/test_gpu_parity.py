@@ -115,6 +115,24 @@ def test_parity_full_size_frame_sampled():
     assert np.mean(gpu["map"][strong]) > 0.95
 
 
+def test_parity_full_size_q32_frame_sampled():
+    """The 2048 x 2048 q = 32 frame (r_b = 4, n = 192, V = 128), FP32 bank, run
+    whole; all velocities compared on every target cell and 512 random cells."""
+    import torch
+    from gpu_common import run_sampled
+    from paper_1604_03622_b300.runner import KStap
+    wl = gen.WORKLOADS["precision2048"]
+    f = gen.make_frame(wl)
+    tcells = [r * wl.W + c for r, c, _, _ in f.targets]
+    cells = np.unique(np.concatenate([tcells, gen.random_cells(wl, 512, seed=8)]).astype(np.int64))
+    ks = KStap.from_workload(wl, f.bank_a, f.bank_b)
+    gpu = run_sampled(ks, torch.from_numpy(f.Y).cuda(), cells)
+    ks.close()
+    ref = oracle.run_workload(f, cells=cells, want_proj=False)
+    rep = compare(gpu, ref, np.arange(len(cells)), wl.tau)
+    print(rep)
+
+
 def test_deterministic_repeat():
     wl = _wl("frame1024", 20, 50)
     f = gen.make_frame(wl)
