@@ -92,78 +92,132 @@ __global__ void k_lrk_tmat(const double2* __restrict__ G, int n, int p, double2*
   Tm[e] = acc;
 }
 
-// Cyclic Jacobi on a Hermitian p x p matrix (FP64, row-major in `A`); on
-// return w holds the eigenvalues in decreasing order and the columns of U
-// (row-major) the eigenvectors.  Off-diagonal entries at or below the
-// matrix's rounding level (1e-16 of sum |A_ii|) are set to zero instead of
-// rotated: without that floor the entries between eigenvalues near zero
-// (a rank-one A has p - 1 of them) keep the sweeps going to the cap.
-__device__ void lrk_jacobi(double2* A, int p, double* w, double2* U) {
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) U[i * p + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+// Cyclic Jacobi on a Hermitian p x p matrix (FP64, row-major in `A`, shared
+// memory), run by the 32 lanes of one warp: each sweep visits the p(p-1)/2
+// pairs in n - 1 rounds of n/2 disjoint pairs (n = p rounded up to even; the
+// round-robin tournament order), so a round's rotation angles are computed
+// side by side (one lane per pair) and its updates of A = G^H A G and U = U G
+// run one lane per (row or column, pair).  On return w holds the eigenvalues
+// in decreasing order and the columns of U (row-major) the eigenvectors.
+// Off-diagonal entries at or below the matrix's rounding level (1e-16 of
+// sum |A_ii|) are set to zero instead of rotated: without that floor the
+// entries between eigenvalues near zero (a rank-one A has p - 1 of them)
+// keep the sweeps going to the cap.  Every lane returns with the same w and U.
+__device__ void lrk_jacobi_warp(double2* A, int p, double* w, double2* U, int lane) {
+  __shared__ double rc[kLrkMaxP / 2], rs[kLrkMaxP / 2];
+  __shared__ double2 rph[kLrkMaxP / 2];
+  __shared__ int ra[kLrkMaxP / 2], rb[kLrkMaxP / 2], rk[kLrkMaxP / 2];   // pair, kind
+  const int n = p + (p & 1), np2 = n / 2;
+  for (int e = lane; e < p * p; e += 32) U[e] = make_double2(e / p == e % p ? 1.0 : 0.0, 0.0);
+  __syncwarp();
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, diag = 0.0, tr = 0.0;
-    for (int i = 0; i < p; ++i) {
-      diag += A[i * p + i].x * A[i * p + i].x;
-      tr += fabs(A[i * p + i].x);
-      for (int j = i + 1; j < p; ++j) off += zabs2(A[i * p + j]);
+    for (int e = lane; e < p * p; e += 32) {
+      const int i = e / p, j = e % p;
+      if (i == j) {
+        diag += A[e].x * A[e].x;
+        tr += fabs(A[e].x);
+      } else if (j > i) {
+        off += zabs2(A[e]);
+      }
     }
-    if (off <= 1e-30 * diag || off == 0.0) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      diag += __shfl_xor_sync(0xffffffffu, diag, o);
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    if (off <= 1e-30 * diag || off == 0.0) break;   // warp-uniform
     const double floor_ab = 1e-16 * tr;
-    for (int a = 0; a < p - 1; ++a)
-      for (int b = a + 1; b < p; ++b) {
-        const double2 apq = A[a * p + b];
-        const double ab = hypot(apq.x, apq.y);   // no squaring: no underflow for tiny entries
-        if (!(ab > fmax(1e-20 * (fabs(A[a * p + a].x) + fabs(A[b * p + b].x)), floor_ab))) {
-          A[a * p + b] = A[b * p + a] = make_double2(0.0, 0.0);
-          continue;
+    for (int round = 0; round < n - 1; ++round) {
+      if (lane < np2) {
+        // pair `lane` of the round: player 0 fixed, the others rotate
+        auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (n - 1); };
+        int a = pos(lane), b = pos(n - 1 - lane);
+        if (a > b) {
+          const int tmp = a;
+          a = b;
+          b = tmp;
         }
-        double2 ph = make_double2(apq.x / ab, apq.y / ab);
-        const double pn = 1.0 / sqrt(zabs2(ph));
-        ph = make_double2(ph.x * pn, ph.y * pn);
-        const double tau = (A[b * p + b].x - A[a * p + a].x) / (2.0 * ab);
-        const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
-        const double2 cph = zconj(ph);
-        for (int k = 0; k < p; ++k) {
-          if (k == a || k == b) continue;
-          const double2 akp = A[k * p + a];
-          const double2 x = zmul(cph, A[k * p + b]);
-          const double2 nkp = make_double2(c * akp.x - sn * x.x, c * akp.y - sn * x.y);
-          const double2 nkq = make_double2(sn * akp.x + c * x.x, sn * akp.y + c * x.y);
-          A[k * p + a] = nkp;
-          A[a * p + k] = zconj(nkp);
-          A[k * p + b] = nkq;
-          A[b * p + k] = zconj(nkq);
+        int kind = 0;   // 0 none (dummy player), 1 rotate, 2 drop the entry
+        if (b < p) {
+          const double2 apq = A[a * p + b];
+          const double ab = hypot(apq.x, apq.y);   // no squaring: no underflow for tiny entries
+          const double App = A[a * p + a].x, Aqq = A[b * p + b].x;
+          if (!(ab > fmax(1e-20 * (fabs(App) + fabs(Aqq)), floor_ab))) {
+            kind = 2;
+          } else {
+            kind = 1;
+            double2 ph = make_double2(apq.x / ab, apq.y / ab);
+            const double pn = 1.0 / sqrt(zabs2(ph));
+            ph = make_double2(ph.x * pn, ph.y * pn);
+            const double tau = (Aqq - App) / (2.0 * ab);
+            const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            rc[lane] = c;
+            rs[lane] = t * c;
+            rph[lane] = zconj(ph);
+          }
         }
-        A[a * p + a] = make_double2(A[a * p + a].x - t * ab, 0.0);
-        A[b * p + b] = make_double2(A[b * p + b].x + t * ab, 0.0);
-        A[a * p + b] = make_double2(0.0, 0.0);
-        A[b * p + a] = make_double2(0.0, 0.0);
-        for (int k = 0; k < p; ++k) {
-          const double2 up = U[k * p + a];
-          const double2 x = zmul(cph, U[k * p + b]);
-          U[k * p + a] = make_double2(c * up.x - sn * x.x, c * up.y - sn * x.y);
-          U[k * p + b] = make_double2(sn * up.x + c * x.x, sn * up.y + c * x.y);
-        }
+        ra[lane] = a;
+        rb[lane] = b;
+        rk[lane] = kind;
       }
+      __syncwarp();
+      // columns a, b of every row (A G, and U G)
+      for (int L = lane; L < p * np2; L += 32) {
+        const int k = L / np2, j = L % np2;
+        if (rk[j] != 1) continue;
+        const int a = ra[j], b = rb[j];
+        const double c = rc[j], sn = rs[j];
+        const double2 cph = rph[j];
+        const double2 xa = A[k * p + a], yb = zmul(cph, A[k * p + b]);
+        A[k * p + a] = make_double2(c * xa.x - sn * yb.x, c * xa.y - sn * yb.y);
+        A[k * p + b] = make_double2(sn * xa.x + c * yb.x, sn * xa.y + c * yb.y);
+        const double2 ua = U[k * p + a], ub = zmul(cph, U[k * p + b]);
+        U[k * p + a] = make_double2(c * ua.x - sn * ub.x, c * ua.y - sn * ub.y);
+        U[k * p + b] = make_double2(sn * ua.x + c * ub.x, sn * ua.y + c * ub.y);
+      }
+      __syncwarp();
+      // rows a, b of every column (G^H (A G))
+      for (int L = lane; L < p * np2; L += 32) {
+        const int k = L / np2, j = L % np2;
+        if (rk[j] != 1) continue;
+        const int a = ra[j], b = rb[j];
+        const double c = rc[j], sn = rs[j];
+        const double2 ph = zconj(rph[j]);
+        const double2 xa = A[a * p + k], yb = zmul(ph, A[b * p + k]);
+        A[a * p + k] = make_double2(c * xa.x - sn * yb.x, c * xa.y - sn * yb.y);
+        A[b * p + k] = make_double2(sn * xa.x + c * yb.x, sn * xa.y + c * yb.y);
+      }
+      __syncwarp();
+      if (lane < np2 && rk[lane] != 0) {   // the rotated (or dropped) entry is zero
+        const int a = ra[lane], b = rb[lane];
+        A[a * p + b] = A[b * p + a] = make_double2(0.0, 0.0);
+        A[a * p + a].y = 0.0;
+        A[b * p + b].y = 0.0;
+      }
+      __syncwarp();
+    }
   }
-  for (int i = 0; i < p; ++i) w[i] = A[i * p + i].x;
-  for (int i = 0; i < p - 1; ++i)
-    for (int j = i + 1; j < p; ++j)
-      if (w[j] > w[i]) {
-        const double tw = w[i];
-        w[i] = w[j];
-        w[j] = tw;
-        for (int k = 0; k < p; ++k) {
-          const double2 u = U[k * p + i];
-          U[k * p + i] = U[k * p + j];
-          U[k * p + j] = u;
+  if (lane == 0) {
+    for (int i = 0; i < p; ++i) w[i] = A[i * p + i].x;
+    for (int i = 0; i < p - 1; ++i)
+      for (int j = i + 1; j < p; ++j)
+        if (w[j] > w[i]) {
+          const double tw = w[i];
+          w[i] = w[j];
+          w[j] = tw;
+          for (int k = 0; k < p; ++k) {
+            const double2 u = U[k * p + i];
+            U[k * p + i] = U[k * p + j];
+            U[k * p + j] = u;
+          }
         }
-      }
+  }
+  __syncwarp();
 }
 
-// A^ = sc vec^-1(a_fin) (row-major complex64 output), sc = p / tr.
 __global__ void k_lrk_aout(const double2* __restrict__ A_fin, const double* __restrict__ info,
                            int p, float2* __restrict__ Aout) {
   const int e = threadIdx.x;
@@ -266,9 +320,9 @@ __global__ void k_lrk_iterate(const double2* __restrict__ Tm, const double2* __r
           Am[m * p + k2] = h;
           Am[k2 * p + m] = zconj(h);
         }
-      lrk_jacobi(Am, p, w, U);
     }
     __syncwarp();
+    lrk_jacobi_warp(Am, p, w, U, lane);
     for (int e = lane; e < p2; e += 32) {   // U = Ub W
       const int i = e / p, m = e % p;
       double2 acc = make_double2(0.0, 0.0);
