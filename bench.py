@@ -228,6 +228,11 @@ TRAFFIC = {
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
         bytes=2 * (1.263921e9 + 0.387137e9),
+        # issue slots used (smsp__issue_active) and FMA-pipe activity of the
+        # same capture: the kernel's float-float arithmetic costs ~10
+        # instructions per algorithmic flop, so issue, not FP32 flops, is its
+        # ceiling
+        issue_active=0.685, fma_pipe_active=0.496,
         sha256="2af87376425e87b5c2a9af884af8c5afb8f18a517fdaed5d8dcafca67c38356e",
         source="profiles/frame1024_512x1024_kernels.md"),
 }
@@ -242,15 +247,15 @@ def measured_peak(key: str):
         return None
 
 
-def measured_traffic(workload: str, precision: str, kernel: str):
+def measured_traffic(workload: str, precision: str, kernel: str, key: str = "bytes"):
     import hashlib
     t = TRAFFIC.get((workload, precision, kernel))
-    if t is None:
+    if t is None or key not in t:
         return None, None
     with open(KERNEL_SRC, "rb") as fh:
         if hashlib.sha256(fh.read()).hexdigest() != t["sha256"]:
             return None, "kernel source changed since the capture"
-    return t["bytes"], t["source"]
+    return t[key], t["source"]
 
 
 # ------------------------------------------------------- batched vs plain ---
@@ -757,6 +762,9 @@ def main():
     roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak_max, unit="TFLOP/s",
                 frac=achieved / peak_max, frac_at_measured_clock=achieved / peak_clock,
                 traffic=traffic_bytes, traffic_source=traffic_src,
+                issue_active_ncu=measured_traffic(wl.name, args.precision, dom, "issue_active")[0],
+                fma_pipe_active_ncu=measured_traffic(wl.name, args.precision, dom,
+                                                     "fma_pipe_active")[0],
                 peak_note="148 SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock); "
                           "no measured FP32 peak in MEASURED_PEAKS.json",
                 kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()},
