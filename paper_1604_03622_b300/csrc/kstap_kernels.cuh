@@ -39,6 +39,7 @@ constexpr int kTileCells = 32;      // cells of one range row per CTA (moments /
 constexpr int kThreads = 256;
 constexpr int kRbMax = 4;
 constexpr float kBlindRefine = 1e-3f;   // |F_B b|^2 / |b|^2 below which w_b is refined in float-float
+constexpr int kBlindQ = 32;             // near-blind (cell, velocity) pairs queued per warp and pass
 constexpr float kLagNorm = 8.673617379884035e-19f;   // 2^-60: integer lag sums -> O(1) floats
 
 struct Geom {
@@ -1286,6 +1287,11 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float* na = reinterpret_cast<float*>(bT + Q * V);    // [V]
   float* nb = na + V;                                  // [V]
   float2* scr = reinterpret_cast<float2*>(na + 2 * V);
+  // near-blind queue of each warp: per pair, G in (R entries) then y (P
+  // entries) and |w_b|^2 out, and the packed (velocity, cell slot)
+  constexpr int QS = (R > P + 1) ? R : P + 1;
+  float2* qd_all = scr + CPB * CS;                                  // [warps][kBlindQ][QS]
+  int* qi_all = reinterpret_cast<int*>(qd_all + (kThreads / 32) * kBlindQ * QS);
   for (int i = threadIdx.x; i < P * V; i += blockDim.x) aT[i] = bank_aT[i];
   for (int i = threadIdx.x; i < Q * V; i += blockDim.x) bT[i] = bank_bT[i];
   for (int i = threadIdx.x; i < 2 * V; i += blockDim.x) na[i] = bank_n2[i];
@@ -1423,7 +1429,12 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   __syncwarp();
   float best = -1.f;
   int bestv = 0x7fffffff;
-  if (live) {
+  float2* qd = qd_all + warp * kBlindQ * QS;
+  int* qi = qi_all + warp * kBlindQ;
+  {
+    // every lane of the warp runs the bank loop (a dead cell's group computes
+    // on its stale scratch and writes nothing), so the near-blind queue below
+    // can use warp-wide votes and shuffles.
     // lane gl takes velocities base + k G + gl: the lanes of a group read
     // consecutive bank words, and each lane still visits its v in increasing
     // order (lowest v wins ties)
@@ -1479,35 +1490,114 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       // Nearly blind velocities (|F_B b|^2 < 1e-3 |b|^2): redo w_b = b - U G with
       // the subtraction in float-float and the low part of U_B included.  Errors
       // of G itself lie in span(U_B), which Z annihilates, so G stays FP32.
+      // The warp queues its (cell, velocity) pairs and refines each with a
+      // group of G lanes (lane j owns w_b[j]) instead of one lane looping over
+      // j while the others wait; pairs past the queue's capacity are refined
+      // by their own lane.
+      auto refine_serial = [&](int k) {
+        const int v = base + k * G + gl;
+        float dBn = 0.f;
+#pragma unroll
+        for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
+        for (int j = 0; j < Q; ++j) {
+          const float2 b = bT[j * V + v];
+          float sr = b.x, cr = 0.f, si = b.y, ci = 0.f;
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            const float2 u = Uh[j * R + m], ul = Ul[j * R + m], G_ = Gm[k][m];
+            acc_prod(sr, cr, -u.x, G_.x);   // re -= ur Gr - ui Gi
+            acc_prod(sr, cr, u.y, G_.y);
+            acc_prod(si, ci, -u.x, G_.y);   // im -= ur Gi + ui Gr
+            acc_prod(si, ci, -u.y, G_.x);
+            cr = __fmaf_rn(-ul.x, G_.x, cr);
+            cr = __fmaf_rn(ul.y, G_.y, cr);
+            ci = __fmaf_rn(-ul.x, G_.y, ci);
+            ci = __fmaf_rn(-ul.y, G_.x, ci);
+          }
+          const float2 w = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+          dBn += cabs2(w);
+#pragma unroll
+          for (int i = 0; i < P; ++i) y[k][i] = cadd(y[k][i], cmul(Zs[i * Q + j], cconj(w)));
+        }
+        dB[k] = dBn;
+      };
+      int qpos[VB];
+      int nq = 0;
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
-        if (base + k * G + gl < V && dB[k] < kBlindRefine * nb[base + k * G + gl]) {
-          float dBn = 0.f;
+        const int v = base + k * G + gl;
+        const bool fl = live && v < V && dB[k] < kBlindRefine * nb[v];
+        const unsigned bal = __ballot_sync(0xffffffffu, fl);
+        qpos[k] = -1;
+        if (fl) {
+          const int pos = nq + __popc(bal & ((1u << lane) - 1u));
+          if (pos < kBlindQ) {
+            qpos[k] = pos;
+            qi[pos] = v | (sub << 16);
 #pragma unroll
-          for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
-          for (int j = 0; j < Q; ++j) {
-            const float2 b = bT[j * V + base + k * G + gl];
-            float sr = b.x, cr = 0.f, si = b.y, ci = 0.f;
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-              const float2 u = Uh[j * R + m], ul = Ul[j * R + m], G = Gm[k][m];
-              acc_prod(sr, cr, -u.x, G.x);   // re -= ur Gr - ui Gi
-              acc_prod(sr, cr, u.y, G.y);
-              acc_prod(si, ci, -u.x, G.y);   // im -= ur Gi + ui Gr
-              acc_prod(si, ci, -u.y, G.x);
-              cr = __fmaf_rn(-ul.x, G.x, cr);
-              cr = __fmaf_rn(ul.y, G.y, cr);
-              ci = __fmaf_rn(-ul.x, G.y, ci);
-              ci = __fmaf_rn(-ul.y, G.x, ci);
-            }
-            const float2 w = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
-            dBn += cabs2(w);
-#pragma unroll
-            for (int i = 0; i < P; ++i) y[k][i] = cadd(y[k][i], cmul(Zs[i * Q + j], cconj(w)));
+            for (int m = 0; m < R; ++m) qd[pos * QS + m] = Gm[k][m];
+          } else {
+            qpos[k] = -2;
           }
-          dB[k] = dBn;
+        }
+        nq += __popc(bal);
+      }
+      nq = min(nq, kBlindQ);
+      __syncwarp();
+      for (int i0 = 0; i0 < nq; i0 += CPW) {   // warp-uniform
+        const int it = i0 + sub;
+        const bool act = it < nq;
+        float2 yv[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) yv[i] = make_float2(0.f, 0.f);
+        float dBn = 0.f;
+        if (act) {
+          const int v = qi[it] & 0xffff, cs = qi[it] >> 16;
+          const float2* sc = scr + (warp * CPW + cs) * CS;
+          const float2* Zc = sc + P * Q;
+          const float2* Uhc = sc + 2 * P * Q;
+          const float2* Ulc = Uhc + Q * R;
+          const int j = gl;
+          const float2 b = bT[j * V + v];
+          float sr = b.x, cr = 0.f, si = b.y, ci = 0.f;
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            const float2 u = Uhc[j * R + m], ul = Ulc[j * R + m], G_ = qd[it * QS + m];
+            acc_prod(sr, cr, -u.x, G_.x);
+            acc_prod(sr, cr, u.y, G_.y);
+            acc_prod(si, ci, -u.x, G_.y);
+            acc_prod(si, ci, -u.y, G_.x);
+            cr = __fmaf_rn(-ul.x, G_.x, cr);
+            cr = __fmaf_rn(ul.y, G_.y, cr);
+            ci = __fmaf_rn(-ul.x, G_.y, ci);
+            ci = __fmaf_rn(-ul.y, G_.x, ci);
+          }
+          const float2 w = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+          dBn = cabs2(w);
+#pragma unroll
+          for (int i = 0; i < P; ++i) yv[i] = cmul(Zc[i * Q + j], cconj(w));
+        }
+        dBn = grp_sum<G>(dBn);
+#pragma unroll
+        for (int i = 0; i < P; ++i) yv[i] = grp_sum2<G>(yv[i]);
+        if (act && gl == 0) {
+#pragma unroll
+          for (int i = 0; i < P; ++i) qd[it * QS + i] = yv[i];
+          qd[it * QS + P] = make_float2(dBn, 0.f);
         }
       }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < VB; ++k) {
+        if (qpos[k] >= 0) {
+#pragma unroll
+          for (int i = 0; i < P; ++i) y[k][i] = qd[qpos[k] * QS + i];
+          dB[k] = qd[qpos[k] * QS + P].x;
+        } else if (qpos[k] == -2) {
+          refine_serial(k);
+        }
+      }
+      __syncwarp();
 
 #pragma unroll
       for (int k = 0; k < VB; ++k) {
@@ -1552,7 +1642,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
         // non-negative terms (no cancellation)
         const float den = classical ? na[v] * dB[k] + dA * fmaxf(nb[v] - dB[k], 0.f) : dA * dB[k];
         const float T = (den < 1e-12f * na[v] * nb[v]) ? 0.f : cabs2(num) / den;
-        if (T_all) T_all[cell * V + v] = T;
+        if (T_all && live) T_all[cell * V + v] = T;
         if (T > best) {
           best = T;
           bestv = v;
