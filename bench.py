@@ -223,17 +223,17 @@ def work_per_cell(wl):
 # source it was taken on: the bench reports null once the file changes.
 KERNEL_SRC = os.path.join(ROOT, "paper_1604_03622_b300", "csrc", "kstap_kernels.cuh")
 TRAFFIC = {
-    # 512 x 1024-cell capture (1.264 GB read + 0.387 GB write) x 2 for the 1024^2
+    # 512 x 1024-cell capture (1.263 GB read + 0.387 GB write) x 2 for the 1024^2
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.263921e9 + 0.387137e9),
+        bytes=2 * (1.262684e9 + 0.387306e9),
         # issue slots used (smsp__issue_active) and FMA-pipe activity of the
         # same capture: the kernel's float-float arithmetic costs ~10
         # instructions per algorithmic flop, so issue, not FP32 flops, is its
         # ceiling
-        issue_active=0.685, fma_pipe_active=0.496,
-        sha256="2af87376425e87b5c2a9af884af8c5afb8f18a517fdaed5d8dcafca67c38356e",
+        issue_active=0.685, fma_pipe_active=0.495,
+        sha256="31b1a216ca2de4b08215dca9926db6fab951643876eadc2fc10dea739db9293a",
         source="profiles/frame1024_512x1024_kernels.md"),
 }
 
