@@ -1046,13 +1046,50 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
 #pragma unroll
       for (int mp = 0; mp < R; ++mp)
         Hh[m][mp] = make_float2(0.5f * (H[m][mp].x + H[mp][m].x), 0.5f * (H[m][mp].y - H[mp][m].y));
-    float dd[R];
-    float2 UU[R][R];
-    // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
-    // by ~1e-10 lambda_1^2 / gap
-    jacobi_small<R, false>(Hh, dd, UU, 1e-10f);
+    if constexpr (R == 1) {
+      lam[0] = Hh[0][0].x;
+    } else if constexpr (R == 2) {
+      // the larger root directly, the smaller as det / larger (no cancellation)
+      const float a = Hh[0][0].x, d = Hh[1][1].x, h = 0.5f * (a - d), m = 0.5f * (a + d);
+      const float r = sqrtf(h * h + cabs2(Hh[0][1]));
+      const float det = a * d - cabs2(Hh[0][1]);
+      lam[0] = m + r;
+      lam[1] = (m + r != 0.f) ? det / (m + r) : m - r;
+    } else if constexpr (R == 3) {
+      // closed form (trigonometric solution of the characteristic cubic of
+      // the shifted, scaled matrix (H - q I) / p, q = tr H / 3): the three
+      // Ritz values are well separated relative to the largest here, so its
+      // single-precision rounding is far inside the tolerance of lambda_B
+      const float a11 = Hh[0][0].x, a22 = Hh[1][1].x, a33 = Hh[2][2].x;
+      const float2 a12 = Hh[0][1], a13 = Hh[0][2], a23 = Hh[1][2];
+      const float q = (a11 + a22 + a33) * (1.f / 3.f);
+      const float b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
+      const float s12 = cabs2(a12), s13 = cabs2(a13), s23 = cabs2(a23);
+      const float p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (s12 + s13 + s23);
+      if (!(p2 > 0.f)) {
+        lam[0] = lam[1] = lam[2] = q;
+      } else {
+        const float p = sqrtf(p2 * (1.f / 6.f));
+        const float2 t = cmul(a12, a23);
+        const float det = b11 * b22 * b33 + 2.f * (t.x * a13.x + t.y * a13.y) - b11 * s23 -
+                          b22 * s13 - b33 * s12;   // det(H - q I)
+        const float r = fminf(1.f, fmaxf(-1.f, det / (2.f * p * p * p)));
+        const float phi = acosf(r) * (1.f / 3.f);
+        const float l1 = q + 2.f * p * cosf(phi);
+        const float l3 = q + 2.f * p * cosf(phi + 2.0943951f);   // + 2 pi / 3
+        lam[0] = l1;
+        lam[1] = 3.f * q - l1 - l3;
+        lam[2] = l3;
+      }
+    } else {
+      float dd[R];
+      float2 UU[R][R];
+      // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
+      // by ~1e-10 lambda_1^2 / gap
+      jacobi_small<R, false>(Hh, dd, UU, 1e-10f);
 #pragma unroll
-    for (int m = 0; m < R; ++m) lam[m] = dd[m];
+      for (int m = 0; m < R; ++m) lam[m] = dd[m];
+    }
   }
 #pragma unroll
   for (int m = 0; m < R; ++m) {
