@@ -227,13 +227,13 @@ TRAFFIC = {
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.262684e9 + 0.387306e9),
+        bytes=2 * (1.262924e9 + 0.387111e9),
         # issue slots used (smsp__issue_active) and FMA-pipe activity of the
         # same capture: the kernel's float-float arithmetic costs ~10
         # instructions per algorithmic flop, so issue, not FP32 flops, is its
         # ceiling
-        issue_active=0.685, fma_pipe_active=0.495,
-        sha256="31b1a216ca2de4b08215dca9926db6fab951643876eadc2fc10dea739db9293a",
+        issue_active=0.689, fma_pipe_active=0.504,
+        sha256="bc5f246e7e82a899f1b21e01ec2c54e069bc3812f7430ef97a71bbd82720a469",
         source="profiles/frame1024_512x1024_kernels.md"),
 }
 
