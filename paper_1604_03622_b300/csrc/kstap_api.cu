@@ -401,7 +401,7 @@ size_t smem_bfit(const Geom& g, bool from_store) {
   const int P = g.p, PP = P * P, Q = g.q, TC = g.tc, R = g.r_b;
   const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
   size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
-  b += (size_t)TC * PP * 8;
+  b += (size_t)TC * PP * 16;
   // the eigen phase's basis scratch reuses the (then dead) lag and box-sum
   // buffers; the lag store is read through two buffers (prefetch of the next lag)
   const size_t vs = (size_t)(kstap::bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;

@@ -118,6 +118,38 @@ __device__ __forceinline__ void acc_ffxff(float& s, float& c, float xh, float xl
   c = __fmaf_rn(xl, yh, c);
 }
 
+// ------------------------------------------------------- packed pairs ------
+// Two independent single-precision lanes per instruction (f32x2, sm_100 and
+// later).  Each lane is rounded exactly as the scalar __f*_rn operation.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  unsigned long long A, B, D;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(D));
+  return r;
+}
+
+// acc_ffxf on a pair of lanes: S + C += (XH + XL) * Y per lane, with
+// NXH = -XH.  The product error comes as -e = p - XH Y (exact), so no lane
+// needs a separate negation; every lane's result equals the scalar acc_ffxf
+// bit for bit.
+__device__ __forceinline__ void acc_ffxf2(float2& S, float2& C, float2 XH, float2 NXH,
+                                          float2 XL, float2 Y) {
+  const float2 p = f2_mul(XH, Y);
+  const float2 ne = f2_fma(NXH, Y, p);            // p - XH Y
+  const float2 t = f2_add(S, p);                  // two_sum(S, p)
+  const float2 bb = f2_sub(t, S);
+  const float2 f = f2_add(f2_sub(S, f2_sub(t, bb)), f2_sub(p, bb));
+  S = t;
+  C = f2_add(C, f2_sub(f, ne));
+  C = f2_fma(XL, Y, C);
+}
+
 // ------------------------------------------------------------ complex ------
 struct cff {
   ff re, im;

@@ -334,7 +334,7 @@ constexpr int kHChunk = 3;                          // positions per item in the
 // W <- W + conj(Pi W Pi^T), s <- s + conj(Pi s) (linear, so per-thread partial
 // sums may be folded before they are complete).
 // Lag store (optional, Lw != nullptr): the exact lag sums of every cell row,
-// as float-float complex (re_hi, re_lo, im_hi, im_lo), laid out
+// as float-float complex (re_hi, im_hi, re_lo, im_lo), laid out
 // Lw[((row * Q + g) * PP + J) * WL + u], WL = W + Q - 1, so that the B pass
 // reads them instead of recomputing them.  Each tile writes positions
 // u in [c0, c0 + TC) (the last tile also its halo).
@@ -486,9 +486,9 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
             L.y += a.y - b.y - c.y + d.y;
           }
           float4 v;
-          ll_to_ff(L.x, v.x, v.y);
-          ll_to_ff(L.y, v.z, v.w);
-          if constexpr (kThreadM) lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.z);
+          ll_to_ff(L.x, v.x, v.z);
+          ll_to_ff(L.y, v.y, v.w);
+          if constexpr (kThreadM) lag[((size_t)t * PP + J) * NUmax + u] = make_float2(v.x, v.y);
           if (Lw && (u < TC || last_tile) && c0 + u < WL && r0 + t < g.H)
             Lw[(((size_t)(r0 + t) * Q + lagg) * PP + J) * WL + c0 + u] = v;
         }
@@ -849,7 +849,7 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
 // ------------------------------------------------ K3: B and U_B ------------
 // B(j, l) of one cell, float-float upper triangle stored by diagonal:
 // diagonal d = l - j >= 0 at offset d*Q - d(d-1)/2, entry j.  float4 =
-// (re_hi, re_lo, im_hi, im_lo).  Lower entries are conjugates.
+// (re_hi, im_hi, re_lo, im_lo).  Lower entries are conjugates.
 template <int Q>
 __host__ __device__ constexpr int diag_off(int d) { return d * Q - (d * (d - 1)) / 2; }
 
@@ -857,7 +857,7 @@ template <int Q>
 __device__ __forceinline__ float4 b_at(const float4* __restrict__ Bc, int j, int l) {
   if (l >= j) return Bc[diag_off<Q>(l - j) + j];
   const float4 v = Bc[diag_off<Q>(j - l) + l];
-  return make_float4(v.x, v.y, -v.z, -v.w);
+  return make_float4(v.x, -v.y, v.z, -v.w);
 }
 
 // Row j of B times the q x R matrix Vs (column-major, [m][l]: lanes read
@@ -872,7 +872,7 @@ __device__ __forceinline__ void b_times_v_fp32(const float4* __restrict__ Bc, in
   for (int t = 0; t < Q; ++t) {
     const int l = (j + t) & (Q - 1);
     const float4 b = b_at<Q>(Bc, j, l);
-    const float2 bh = make_float2(b.x, b.z);
+    const float2 bh = make_float2(b.x, b.y);
 #pragma unroll
     for (int m = 0; m < R; ++m) y[m] = cadd(y[m], cmul(bh, Vs[m * Q + l]));
   }
@@ -933,7 +933,7 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const float4 b = b_at<Q>(Bc, j, ((2 * m + 1) * Q) / (2 * R));
-    v[m] = make_float2(b.x, b.z);
+    v[m] = make_float2(b.x, b.y);
   }
   orthonormalise_g<Q, R>(v);
 #pragma unroll
@@ -954,26 +954,34 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
 #pragma unroll
     for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
     __syncwarp();
-    float s[R][4];
+    // packed pairs: (re, im) += (br, bi) xr and (x, y) += (br, bi) (xi, -xi),
+    // then re = re1 + y, im = im1 + x (error-free merge)
+    float2 s1[R], c1[R], s2[R], c2[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) s[m][0] = s[m][1] = s[m][2] = s[m][3] = 0.f;
+    for (int m = 0; m < R; ++m) s1[m] = c1[m] = s2[m] = c2[m] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int t = 0; t < Q; ++t) {
       const int l = (j + t) & (Q - 1);
       const float4 b = b_at<Q>(Bc, j, l);
+      const float2 xh = make_float2(b.x, b.y), xl = make_float2(b.z, b.w);
+      const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const float2 x = Vs[m * Q + l];
-        acc_ffxf(s[m][0], s[m][1], b.x, b.y, x.x);     // re = br xr - bi xi
-        acc_ffxf(s[m][0], s[m][1], b.z, b.w, -x.y);
-        acc_ffxf(s[m][2], s[m][3], b.x, b.y, x.y);     // im = br xi + bi xr
-        acc_ffxf(s[m][2], s[m][3], b.z, b.w, x.x);
+        acc_ffxf2(s1[m], c1[m], xh, nxh, xl, make_float2(x.x, x.x));
+        acc_ffxf2(s2[m], c2[m], xh, nxh, xl, make_float2(x.y, -x.y));
       }
     }
     __syncwarp();
     cff Yf[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) Yf[m] = cff{ff_make(s[m][0], s[m][1]), ff_make(s[m][2], s[m][3])};
+    for (int m = 0; m < R; ++m) {
+      float sr, er, si, ei;
+      two_sum(s1[m].x, s2[m].y, sr, er);
+      two_sum(s1[m].y, s2[m].x, si, ei);
+      Yf[m] = cff{ff_make(sr, __fadd_rn(er, __fadd_rn(c1[m].x, c2[m].y))),
+                  ff_make(si, __fadd_rn(ei, __fadd_rn(c1[m].y, c2[m].x)))};
+    }
     // H = V^H Y (FP32), Gram G = Y^H Y (float-float)
 #pragma unroll
     for (int m = 0; m < R; ++m)
@@ -1117,30 +1125,26 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // One B entry, float-float: sum_J conj(a_J) L_J with a single precision and L
-// float-float (re_hi, re_lo, im_hi, im_lo).  With NCH = 2, even and odd J
-// accumulate in separate compensated sums (two independent dependency
-// chains, for CTAs whose threads hold one entry each), merged at the end with
-// an error-free two_sum.
-template <int NCH>
+// float-float (re_hi, im_hi, re_lo, im_lo), on packed pairs: (re, im) +=
+// (Lr, Li) ar and (x, y) += (Lr, Li) (-ai, ai) run as two compensated pair
+// sums (two independent dependency chains), merged at the end with an
+// error-free two_sum: re = re1 + y, im = im1 + x.  ya = (ar, ar, -ai, ai).
 struct BAcc {
-  float sr[2] = {0.f, 0.f}, cr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f}, ci[2] = {0.f, 0.f};
-  __device__ __forceinline__ void add(int k, float2 a, float4 L) {
-    acc_ffxf(sr[k], cr[k], L.x, L.y, a.x);     // conj(a) L: re = ar Lr + ai Li
-    acc_ffxf(sr[k], cr[k], L.z, L.w, a.y);
-    acc_ffxf(si[k], ci[k], L.z, L.w, a.x);     //            im = ar Li - ai Lr
-    acc_ffxf(si[k], ci[k], L.x, L.y, -a.y);
+  float2 s1 = {0.f, 0.f}, c1 = {0.f, 0.f}, s2 = {0.f, 0.f}, c2 = {0.f, 0.f};
+  __device__ __forceinline__ void add(float4 ya, float4 L) {
+    const float2 xh = make_float2(L.x, L.y), xl = make_float2(L.z, L.w);
+    const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
+    acc_ffxf2(s1, c1, xh, nxh, xl, make_float2(ya.x, ya.y));
+    acc_ffxf2(s2, c2, xh, nxh, xl, make_float2(ya.z, ya.w));
   }
+  // (re_hi, im_hi, re_lo, im_lo), the layout of the tile's B entries
   __device__ __forceinline__ float4 get() const {
-    if (NCH == 1) {
-      const ff re = ff_make(sr[0], cr[0]), im = ff_make(si[0], ci[0]);
-      return make_float4(re.hi, re.lo, im.hi, im.lo);
-    }
     float s, e;
-    two_sum(sr[0], sr[1], s, e);
-    const ff re = ff_make(s, __fadd_rn(e, __fadd_rn(cr[0], cr[1])));
-    two_sum(si[0], si[1], s, e);
-    const ff im = ff_make(s, __fadd_rn(e, __fadd_rn(ci[0], ci[1])));
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+    two_sum(s1.x, s2.y, s, e);
+    const ff re = ff_make(s, __fadd_rn(e, __fadd_rn(c1.x, c2.y)));
+    two_sum(s1.y, s2.x, s, e);
+    const ff im = ff_make(s, __fadd_rn(e, __fadd_rn(c1.y, c2.x)));
+    return make_float4(re.hi, im.hi, re.lo, im.lo);
   }
 };
 
@@ -1177,8 +1181,8 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   const int NUmax = TC + Q - 1;
   const size_t ncell = (size_t)JL.NC;
   float4* Bs = reinterpret_cast<float4*>(smem);                 // [TC][NB]
-  float2* as = reinterpret_cast<float2*>(Bs + TC * NB);         // [TC][PP]
-  float4* lag = reinterpret_cast<float4*>(as + TC * PP);        // [kLagStages or 1][PP][NUmax]
+  float4* as = Bs + TC * NB;                                    // [TC][PP] (ar, ar, -ai, ai)
+  float4* lag = as + TC * PP;                                   // [kLagStages or 1][PP][NUmax]
   float2* Vs = reinterpret_cast<float2*>(lag);                  // eigen phase: [warps * CPW][Q][R]
   longlong2* Vo = reinterpret_cast<longlong2*>(lag + PP * NUmax);   // recompute only
   longlong2* Vg = Vo + PP * WT;
@@ -1200,27 +1204,45 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
     }
     cp_async_commit();
   };
+  // lag of load position pos in the B-phase order 0, 1, Q-1, 2, Q-2, ..,
+  // Q/2: lags g and Q - g are contracted together, TC * Q entries per pair
+  auto lag_at = [](int pos) { return pos == 0 ? 0 : pos == Q - 1 ? Q / 2 : (pos & 1) ? (pos + 1) / 2 : Q - pos / 2; };
+  int issued = 0;
   if (FROM_STORE) {
-#pragma unroll
-    for (int st = 0; st < kLagStages; ++st)
-      if (st < Q) prefetch(st, st);
+    for (; issued < kLagStages && issued < Q; ++issued) prefetch(lag_at(issued), issued);
   } else {
     load_tile_q<P>(Y, g, r, c0, WT, scale, Yq);
   }
   for (int idx = threadIdx.x; idx < TC * PP; idx += NT) {
     const int cl = idx / PP, J = idx % PP;
     const int c = c0 + cl;
-    as[idx] = (c < g.W) ? aw[J * ncell + (size_t)JB.cell0 + (size_t)r * g.W + c]
-                        : make_float2(0.f, 0.f);
+    const float2 a = (c < g.W) ? aw[J * ncell + (size_t)JB.cell0 + (size_t)r * g.W + c]
+                               : make_float2(0.f, 0.f);
+    as[idx] = make_float4(a.x, a.x, -a.y, a.y);
   }
   __syncthreads();
 
-  for (int lagg = 0; lagg < Q; ++lagg) {
-    const int NU = TC + Q - 1 - lagg;
-    const float4* lb = lag;
-    if (FROM_STORE) {
-      // groups committed so far: lags 0 .. min(lagg + kLagStages - 1, Q - 1)
-      const int ahead = min(kLagStages - 1, Q - 1 - lagg);
+  // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float, for entry
+  // e = cl * (Q - lag) + j of one lag.  Positions the prefetch zero-filled
+  // are read only by cells past the frame edge.
+  auto b_entry = [&](int lagg, const float4* lb, int e) {
+    const int nj = Q - lagg;
+    const int cl = e / nj, j = e - cl * nj;
+    BAcc b;
+#pragma unroll
+    for (int J = 0; J < PP; ++J) b.add(as[cl * PP + J], lb[J * NUmax + cl + j]);
+    Bs[cl * NB + diag_off<Q>(lagg) + j] = b.get();
+  };
+  if (FROM_STORE) {
+    // Q / 2 + 1 steps: {0}, {1, Q-1}, .., {Q/2-1, Q/2+1}, {Q/2}.  A pair has
+    // TC * Q entries (whole rounds of the CTA where a lag alone leaves most
+    // threads idle at the long lags).  Load positions [p0, p1) of a step sit
+    // in buffers pos % kLagStages; after the step they are refilled with the
+    // next positions, so at most kLagStages - (p1 - p0) groups are in flight.
+    for (int step = 0; step <= Q / 2; ++step) {
+      const int p0 = (step == 0) ? 0 : 2 * step - 1;
+      const int p1 = (step == 0) ? 1 : (step == Q / 2) ? Q : 2 * step + 1;
+      const int ahead = issued - p1;   // groups allowed to stay outstanding, 0 .. 3
       if (ahead >= 3)
         cp_async_wait<3>();
       else if (ahead == 2)
@@ -1229,8 +1251,23 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
         cp_async_wait<1>();
       else
         cp_async_wait<0>();
-      lb = lag + (lagg % kLagStages) * PP * NUmax;
-    } else {
+      __syncthreads();
+      const int la = lag_at(p0), lb_ = lag_at(p1 - 1);
+      const int na = TC * (Q - la);
+      const int tot = (p1 - p0 == 2) ? na + TC * (Q - lb_) : na;
+      const float4* bufa = lag + (p0 % kLagStages) * PP * NUmax;
+      const float4* bufb = lag + ((p1 - 1) % kLagStages) * PP * NUmax;
+      for (int idx = threadIdx.x; idx < tot; idx += NT) {
+        const bool first = idx < na;
+        b_entry(first ? la : lb_, first ? bufa : bufb, first ? idx : idx - na);
+      }
+      __syncthreads();
+      for (; issued < Q && issued < p1 + kLagStages; ++issued)
+        prefetch(lag_at(issued), issued % kLagStages);
+    }
+  } else {
+    for (int lagg = 0; lagg < Q; ++lagg) {
+      const int NU = TC + Q - 1 - lagg;
       const int KW = NU + 2 * g.Ra;
       vertical_sums<P>(Yq, g, WT, lagg, KW, Vo, Vg);
       __syncthreads();
@@ -1238,25 +1275,14 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
         const int u = idx % NU, J = idx / NU;
         const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
         float4 v;
-        ll_to_ff(L.x, v.x, v.y);
-        ll_to_ff(L.y, v.z, v.w);
+        ll_to_ff(L.x, v.x, v.z);
+        ll_to_ff(L.y, v.y, v.w);
         lag[J * NUmax + u] = v;
       }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < TC * (Q - lagg); idx += NT) b_entry(lagg, lag, idx);
+      __syncthreads();
     }
-    __syncthreads();
-    // B(j, j + lag) = sum_J conj(a_J) l_lag(c + j)[J], float-float.  Positions
-    // the prefetch zero-filled are read only by cells past the frame edge.
-    const int nj = Q - lagg, tot = TC * nj;
-    for (int idx = threadIdx.x; idx < tot; idx += NT) {
-      const int cl = idx / nj, j = idx % nj;
-      constexpr int NCH = (Q >= 32) ? 2 : 1;   // q = 32: tot <= NT, one entry per thread
-      BAcc<NCH> b;
-#pragma unroll
-      for (int J = 0; J < PP; ++J) b.add(NCH == 2 ? (J & 1) : 0, as[cl * PP + J], lb[J * NUmax + cl + j]);
-      Bs[cl * NB + diag_off<Q>(lagg) + j] = b.get();
-    }
-    __syncthreads();
-    if (FROM_STORE && lagg + kLagStages < Q) prefetch(lagg + kLagStages, lagg % kLagStages);
   }
 
   // eigen phase: a group of Q lanes per cell
@@ -1281,7 +1307,7 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
       if (j == 0 && lamB) {
         // B^ = b / |a|^2 in S units, then tr A^ = p normalisation
         float an = 0.f, tr = 0.f;
-        for (int J = 0; J < PP; ++J) an += cabs2(as[cl * PP + J]);
+        for (int J = 0; J < PP; ++J) an += cabs2(make_float2(as[cl * PP + J].x, as[cl * PP + J].w));
         for (int i = 0; i < P; ++i) tr += as[cl * PP + i * (P + 1)].x;
         const float unit = ldexpf(1.f, 60 - 2 * sh) / (float)g.n;
         const float f = (an > 0.f) ? unit / an * tr / (float)P : 0.f;

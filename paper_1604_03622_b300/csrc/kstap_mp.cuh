@@ -97,8 +97,7 @@ k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
       while (lg + 1 < Q && ring_off<Q>(lg + 1) <= sl) ++lg;
       const int k = sl - ring_off<Q>(lg);   // position c0 + k
       if (k < Q - lg) {
-        const float4 v = __ldg(rowL + ((size_t)lg * PP + J) * WL + c0 + k);
-        ring[sl * PP + J] = make_float2(v.x, v.z);
+        ring[sl * PP + J] = __ldg(reinterpret_cast<const float2*>(rowL + ((size_t)lg * PP + J) * WL + c0 + k));
       }
     }
     __syncthreads();
@@ -153,8 +152,7 @@ k_mgram(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
         nv[t] = make_float2(0.f, 0.f);
         if (e < NEW) {
           const int lg = e / PP, J = e - lg * PP;
-          const float4 v = __ldg(rowL + ((size_t)lg * PP + J) * WL + c + Q - 1 - lg);
-          nv[t] = make_float2(v.x, v.z);
+          nv[t] = __ldg(reinterpret_cast<const float2*>(rowL + ((size_t)lg * PP + J) * WL + c + Q - 1 - lg));
         }
       }
     };
