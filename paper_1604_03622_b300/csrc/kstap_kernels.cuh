@@ -1507,18 +1507,23 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       for (int k = 0; k < VB; ++k)
 #pragma unroll
         for (int m = 0; m < R; ++m) Gm[k][m] = make_float2(0.f, 0.f);
-      // G = U_B^H b_v
+      // G = U_B^H b_v, on packed pairs: G += (br, bi) ur + (bi, br) (ui, -ui)
 #pragma unroll 4
       for (int j = 0; j < Q; ++j) {
-        float2 u[R];
+        float2 ur[R], ui[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) u[m] = Uh[j * R + m];
+        for (int m = 0; m < R; ++m) {
+          const float2 u = Uh[j * R + m];
+          ur[m] = make_float2(u.x, u.x);
+          ui[m] = make_float2(u.y, -u.y);
+        }
 #pragma unroll
         for (int k = 0; k < VB; ++k) {
           if (base + k * G + gl < V) {
             const float2 b = bT[j * V + base + k * G + gl];
+            const float2 bs = make_float2(b.y, b.x);
 #pragma unroll
-            for (int m = 0; m < R; ++m) Gm[k][m] = cadd(Gm[k][m], cmulc(u[m], b));
+            for (int m = 0; m < R; ++m) Gm[k][m] = f2_fma(bs, ui[m], f2_fma(b, ur[m], Gm[k][m]));
           }
         }
       }
@@ -1531,22 +1536,36 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
 #pragma unroll
         for (int i = 0; i < P; ++i) y[k][i] = make_float2(0.f, 0.f);
       }
+      // on packed pairs: w = b - U G as (br, bi) - G ur and (x, y) = G (-ui, ui),
+      // w = (re + y, im + x); y_i += (zr, zi) wr + (zi, zr) (wi, -wi)
 #pragma unroll 4
       for (int j = 0; j < Q; ++j) {
-        float2 u[R], zz[P];
+        float2 nur[R], nui[R], zz[P], zs[P];
 #pragma unroll
-        for (int m = 0; m < R; ++m) u[m] = Uh[j * R + m];
+        for (int m = 0; m < R; ++m) {
+          const float2 u = Uh[j * R + m];
+          nur[m] = make_float2(-u.x, -u.x);
+          nui[m] = make_float2(-u.y, u.y);
+        }
 #pragma unroll
-        for (int i = 0; i < P; ++i) zz[i] = Zs[i * Q + j];
+        for (int i = 0; i < P; ++i) {
+          zz[i] = Zs[i * Q + j];
+          zs[i] = make_float2(zz[i].y, zz[i].x);
+        }
 #pragma unroll
         for (int k = 0; k < VB; ++k) {
           if (base + k * G + gl < V) {
-            float2 w = bT[j * V + base + k * G + gl];
+            float2 w1 = bT[j * V + base + k * G + gl], w2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int m = 0; m < R; ++m) w = csub(w, cmul(u[m], Gm[k][m]));
-            dB[k] += cabs2(w);
+            for (int m = 0; m < R; ++m) {
+              w1 = f2_fma(Gm[k][m], nur[m], w1);
+              w2 = f2_fma(Gm[k][m], nui[m], w2);
+            }
+            const float wr = w1.x + w2.y, wi = w1.y + w2.x;
+            dB[k] += cabs2(make_float2(wr, wi));
+            const float2 WR = make_float2(wr, wr), WI = make_float2(wi, -wi);
 #pragma unroll
-            for (int i = 0; i < P; ++i) y[k][i] = cadd(y[k][i], cmul(zz[i], cconj(w)));
+            for (int i = 0; i < P; ++i) y[k][i] = f2_fma(zs[i], WI, f2_fma(zz[i], WR, y[k][i]));
           }
         }
       }
