@@ -220,20 +220,32 @@ def work_per_cell(wl):
 
 # DRAM bytes per launch of a kernel on a workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
-# source it was taken on: the bench reports null once the file changes.
-KERNEL_SRC = os.path.join(ROOT, "paper_1604_03622_b300", "csrc", "kstap_kernels.cuh")
+# sources it was taken on: the bench reports null once either file changes.
+KERNEL_SRC = [os.path.join(ROOT, "paper_1604_03622_b300", "csrc", f)
+              for f in ("kstap_kernels.cuh", "kstap_ff.cuh")]
+
+
+def kernel_src_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 TRAFFIC = {
-    # 512 x 1024-cell capture (1.263 GB read + 0.387 GB write) x 2 for the 1024^2
+    # 512 x 1024-cell capture (1.265 GB read + 0.389 GB write) x 2 for the 1024^2
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.262924e9 + 0.387111e9),
+        bytes=2 * (1.264918e9 + 0.388752e9),
         # issue slots used (smsp__issue_active) and FMA-pipe activity of the
         # same capture: the kernel's float-float arithmetic costs ~10
-        # instructions per algorithmic flop, so issue, not FP32 flops, is its
-        # ceiling
-        issue_active=0.689, fma_pipe_active=0.504,
-        sha256="bc5f246e7e82a899f1b21e01ec2c54e069bc3812f7430ef97a71bbd82720a469",
+        # instructions per algorithmic flop (packed f32x2 pairs issue two
+        # lanes at once but hold the FMA pipe for two cycles)
+        issue_active=0.608, fma_pipe_active=0.570,
+        sha256="8edb4f32cf7260193097fbd809e4cfdd899116d1d44fdc91e7d97be12291d87c",
         source="profiles/frame1024_512x1024_kernels.md"),
 }
 
@@ -248,13 +260,11 @@ def measured_peak(key: str):
 
 
 def measured_traffic(workload: str, precision: str, kernel: str, key: str = "bytes"):
-    import hashlib
     t = TRAFFIC.get((workload, precision, kernel))
     if t is None or key not in t:
         return None, None
-    with open(KERNEL_SRC, "rb") as fh:
-        if hashlib.sha256(fh.read()).hexdigest() != t["sha256"]:
-            return None, "kernel source changed since the capture"
+    if kernel_src_sha256() != t["sha256"]:
+        return None, "kernel source changed since the capture"
     return t[key], t["source"]
 
 
