@@ -393,9 +393,10 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
 
   const int tr = threadIdx.x / TC, cl = threadIdx.x % TC;
   const bool live = (c0 + cl) < g.W && (r0 + tr) < g.H;
-  float wr[NE], wi[NE], sr[NS], si[NS];
+  float2 W[NE];   // entries of M (re, im), packed pairs
+  float sr[NS], si[NS];
 #pragma unroll
-  for (int e = 0; e < NE; ++e) wr[e] = wi[e] = 0.f;
+  for (int e = 0; e < NE; ++e) W[e] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int J = 0; J < NS; ++J) sr[J] = si[J] = 0.f;
 
@@ -508,19 +509,19 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
           if (ep < e) continue;                 // each pair once
           if (ep == e) {
             // conj(W[pi J, pi J']) with the same storage slot
-            const float xr = wr[e], xi = (a <= b) ? wi[e] : -wi[e];
-            wr[e] += xr;
-            wi[e] -= xi;
+            const float xr = W[e].x, xi = (a <= b) ? W[e].y : -W[e].y;
+            W[e].x += xr;
+            W[e].y -= xi;
           } else {
             // slot e receives conj(W[a,b]); slot ep receives conj(W[pi a, pi b]) = conj(W[J,J'] or its conj)
-            const float er = wr[e], ei = wi[e], fr = wr[ep], fi = wi[ep];
+            const float er = W[e].x, ei = W[e].y, fr = W[ep].x, fi = W[ep].y;
             const float abr = fr, abi = (a <= b) ? fi : -fi;    // W[a, b]
-            wr[e] = er + abr;
-            wi[e] = ei - abi;
+            W[e].x = er + abr;
+            W[e].y = ei - abi;
             // slot ep holds W[min(a,b), max(a,b)]; pi maps (a,b) back to (J,J')
             const float jr = er, ji = (a <= b) ? ei : -ei;      // W[pi a, pi b] in ep's orientation
-            wr[ep] = fr + jr;
-            wi[ep] = fi - ji;
+            W[ep].x = fr + jr;
+            W[ep].y = fi - ji;
           }
         }
       }
@@ -545,18 +546,23 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     if (live) {
       const float2* lt = lag + (size_t)tr * PP * NUmax;
       for (int j = 0; j < Q - lagg; ++j) {
-        float2 l[PP];
-#pragma unroll
-        for (int J = 0; J < PP; ++J) l[J] = lt[J * NUmax + cl + j];
+        float2 l[PP], lb[PP];
 #pragma unroll
         for (int J = 0; J < PP; ++J) {
+          l[J] = lt[J * NUmax + cl + j];
+          lb[J] = make_float2(l[J].y, -l[J].x);
           sr[J] += l[J].x;
           si[J] += l[J].y;
+        }
+        // W[J][J'] += l[J] conj(l[J']) = (lr, li) l'r + (li, -lr) l'i, column
+        // by column so that only one column's broadcast pairs are live
 #pragma unroll
-          for (int Jp = J; Jp < PP; ++Jp) {
+        for (int Jp = 0; Jp < PP; ++Jp) {
+          const float2 xr = make_float2(l[Jp].x, l[Jp].x), xi = make_float2(l[Jp].y, l[Jp].y);
+#pragma unroll
+          for (int J = 0; J <= Jp; ++J) {
             const int e = tri_idx(PP, J, Jp);
-            wr[e] += l[J].x * l[Jp].x + l[J].y * l[Jp].y;   // l[J] conj(l[J'])
-            wi[e] += l[J].y * l[Jp].x - l[J].x * l[Jp].y;
+            W[e] = f2_fma(lb[J], xi, f2_fma(l[J], xr, W[e]));
           }
         }
       }
@@ -569,7 +575,7 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     const size_t ncell = (size_t)JL.NC;
     const size_t cell = (size_t)JB.cell0 + (size_t)(r0 + tr) * g.W + (c0 + cl);
 #pragma unroll
-    for (int e = 0; e < NE; ++e) Mw[e * ncell + cell] = make_float2(wr[e], wi[e]);
+    for (int e = 0; e < NE; ++e) Mw[e * ncell + cell] = W[e];
 #pragma unroll
     for (int J = 0; J < PP; ++J) Sw[J * ncell + cell] = make_float2(sr[J], si[J]);
   }
