@@ -161,10 +161,13 @@ kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
                           const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
                           float* T_all);
 
-/* Waits for the context stream, then reports whether any kernel on this
- * device gave up a bounded wait for its tensor-core work (KSTAP_ECUDA, with
- * the reason in kstap_last_error; the word is cleared) or not (KSTAP_OK).
- * Results of a launch that gave up are not valid. */
+/* Waits for the context stream, then reports whether a tensor-core kernel of
+ * this context gave up a bounded wait for its MMAs (KSTAP_ECUDA, with the
+ * reason in kstap_last_error; the word is cleared) or not (KSTAP_OK).
+ * Results of a launch that gave up are not valid; if the message says the
+ * device state is unknown, the MMAs had not completed when the kernel freed
+ * their tensor memory, and the process should reset the device
+ * (cudaDeviceReset) before further work. */
 kstap_status kstap_device_status(kstap_ctx* ctx);
 
 /* Free the context, its workspace and its copies of the bank. */
@@ -312,9 +315,10 @@ kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket);
  * rejected with KSTAP_EINVAL and a message from kstap_last_error(NULL); other
  * errors are reported the same way.
  *
- * The first call on each device looks up that device's address of the array
- * (with that device current); make that first call before any stream
- * capture.  Every call shares the one array: calls that overlap on the GPU
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first lookup on a
+ * device also loads the library's device code there, so make the first call
+ * on each device before any stream capture.  Every call shares the one array: calls that overlap on the GPU
  * (different streams, or different host threads, on the same device) race
  * and corrupt each other's results, so serialise them.  The array keeps the
  * last call's contents; the call clears what it needs zeroed itself. */

@@ -3,86 +3,37 @@
 // Every launch works on a job list: one frame passed by value (the per-frame
 // calls) or a device table of frames (batches and CUDA graphs).  Kernels use
 // persistent grids (occupancy x waves CTAs striding over all tiles of all
-// jobs of the launch).
+// jobs of the launch).  The launch sequences of each class (p, q) live in
+// their own translation units (kstap_inst.cu); this file holds the host
+// logic: validation, workspace layout, strips, batches, graphs, the
+// autotuner, serving and the context-free entry points.
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <mutex>
 #include <thread>
 #include <unordered_map>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <mutex>
-#include <string>
-#include <vector>
 
-#include "../../include/kstap.h"
-#include "kstap_kernels.cuh"
-#include "kstap_tc.cuh"
+#include "kstap_host.cuh"
 #include "kstap_lrk.cuh"
-#include "kstap_mp.cuh"
+#include "kstap_misc.cuh"
 
-using kstap::Geom;
-using kstap::Job;
-using kstap::JobList;
-
-struct Server;
-namespace {
-struct Tuning {
-  int waves = 4;   // persistent grid = SMs x resident CTAs x waves (capped by tiles)
-  int tc = 0;      // cells per tile in the B pass (0 = default: 32, or 16 for q = 32)
-};
-}  // namespace
-
-struct kstap_ctx {
-  kstap_params prm;
-  int V = 0;
-  cudaStream_t stream = nullptr;
-  size_t budget = 0;
-  int device = 0;
-  int sm_count = 148;
-  // bank, transposed for the detect kernel: aT [p][V], bT [q][V], norms [2V]
-  float2* bank_aT = nullptr;
-  float2* bank_bT = nullptr;
-  float* bank_n2 = nullptr;
-  // tensor-core route: bank operand image (hi, lo; tcgen05 K-major layout)
-  // and the inverse of its power-of-two scale
-  uint4* bank_op = nullptr;
-  float bank_inv = 1.f;
-  // workspace and the device job table of kstap_run_batch
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  Job* jobs_dev = nullptr;
-  size_t jobs_cap = 0;
-  Tuning tune;
-  std::string err;
-  // optional per-kernel timing: events around every launch on ctx->stream
-  bool profile = false;
-  cudaEvent_t ev[kstap_nkernels + 1][2] = {};
-  float kernel_ms[kstap_nkernels] = {};
-  int kernel_launches[kstap_nkernels] = {};
-  bool ev_pending[kstap_nkernels] = {};
-  struct Server* server = nullptr;   // created by the first kstap_submit
-  // device words: frame scan of kstap_detect (max bits, non-finite flag) and
-  // the counters of the last fit ([0] cells at max_iter, [1] non-finite cells)
-  unsigned* det_flags = nullptr;
-  unsigned long long* report = nullptr;
-};
-
-struct kstap_graph {
-  std::vector<void*> allocs;          // workspaces and job tables owned by the graph
-  std::vector<cudaStream_t> streams;  // capture root and branches
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
+using namespace kh;
 
 namespace {
 
 thread_local std::string g_create_err;
+// Set by the serving worker thread: failures it meets are recorded here
+// instead of in the context, whose error string belongs to the caller's
+// thread.
+thread_local std::string* t_err_sink = nullptr;
+
+}  // namespace
+
+namespace kh {
 
 void prof_begin(kstap_ctx* ctx, int k, cudaStream_t s) {
   if (!ctx || !ctx->profile) return;
@@ -118,19 +69,34 @@ kstap_status fail(kstap_ctx* ctx, kstap_status st, const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
-  if (ctx)
+  if (t_err_sink)
+    *t_err_sink = buf;
+  else if (ctx)
     ctx->err = buf;
   else
     g_create_err = buf;
   return st;
 }
 
-#define KSTAP_CUDA(ctx, call)                                                            \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail((ctx), KSTAP_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
-  } while (0)
+
+// Frame scan of every job: max |component| (fixed-point scale) and the
+// non-finite flag, into each job's maxbits words (zeroed by the caller).
+kstap_status enqueue_scan(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                          int sm_count, cudaStream_t s) {
+  const size_t maxf = JL.table ? 0 : 2 * (size_t)g.p * JL.one.H_in * JL.one.W_in;
+  const int bx = JL.table ? sm_count * 2
+                          : (int)std::min<size_t>((maxf + 1023) / 1024, (size_t)sm_count * 16);
+  prof_collect(prof, KSTAP_K_SCALE);
+  prof_begin(prof, KSTAP_K_SCALE, s);
+  kstap::k_frame_maxabs<<<dim3(std::max(1, bx), JL.njobs), 256, 0, s>>>(g, JL);
+  prof_end(prof, KSTAP_K_SCALE, s);
+  KSTAP_CUDA(ctx, cudaGetLastError());
+  return KSTAP_OK;
+}
+
+}  // namespace kh
+
+namespace {
 
 int ceil_log2(long v) {
   int k = 0;
@@ -230,17 +196,6 @@ Geom make_geom(const kstap_params& p, int V, int tc) {
   return g;
 }
 
-inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Scratch layout of one launch over frames with cell grids H x W: per-job
-// scale words, per-cell arrays (struct of arrays over all cells of all
-// jobs), then the per-job lag stores.
-struct Layout {
-  size_t flags, Mw, Sw, aw, Lw, total;
-  size_t NC;
-  std::vector<size_t> cell0, lag0;   // per job (lag0 in float4 units)
-};
-
 Layout make_layout(const kstap_params& p, const std::vector<std::pair<int, int>>& HW,
                    bool lag_store) {
   const size_t PP = (size_t)p.p * p.p, NE = PP * (PP + 1) / 2;
@@ -260,24 +215,6 @@ Layout make_layout(const kstap_params& p, const std::vector<std::pair<int, int>>
   L.Lw = up256(L.aw + L.NC * PP * sizeof(float2));
   L.total = up256(L.Lw + lag * sizeof(float4));
   return L;
-}
-
-int tiles_moments(int H, int W) {
-  return ((W + kstap::kTileCells - 1) / kstap::kTileCells) *
-         ((H + kstap::kMomRows - 1) / kstap::kMomRows);
-}
-int tiles_flip(int H, int W, int p = 3) {
-  const size_t per = p <= 3 ? 128 : kstap::kFlipThreads;   // a thread per cell
-  return (int)(((size_t)H * W + per - 1) / per);
-}
-int tiles_mgram(int H, int W, int p) {
-  return p <= 3 ? 0 : ((W + kstap::kStrip - 1) / kstap::kStrip) * H;   // a CTA per strip
-}
-int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
-int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
-int tiles_detect(int H, int W, int q, int precision = KSTAP_FP32) {
-  const int c = precision == KSTAP_FP32 ? cells_per_detect_block(q) : kstap::kTcCells;
-  return (int)(((size_t)H * W + c - 1) / c);
 }
 
 // A frame (or a row strip of one) as the library sees it (device pointers,
@@ -375,55 +312,6 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
   JL.NC = L ? (long long)L->NC : 0;
 }
 
-size_t smem_moments(const Geom& g) {
-  const int P = g.p, PP = P * P, TC = kstap::kTileCells, TR = kstap::kMomRows;
-  const int NRT = 2 * g.Rr + TR, WT = TC + 2 * g.Ra + g.q - 1, NUmax = TC + g.q - 1;
-  size_t b = (size_t)P * NRT * WT * 8;
-  b += (b & 15);
-  b += 2 * (size_t)PP * WT * 16;
-  if (P <= 3) b += (size_t)TR * PP * NUmax * 8;   // row lags for the per-thread M
-  return b;
-}
-
-size_t smem_mgram(const Geom& g) {
-  // the lag windows' ring (sum_g (q - g + 1) slots of PP entries), the fold
-  // scratch and the block sums
-  const size_t PP = (size_t)g.p * g.p, slots = (size_t)g.q * (g.q + 3) / 2;
-  return (slots * PP + PP * PP + PP) * 8;
-}
-
-size_t smem_flipt(const Geom& g) {
-  // a, y = M a and the two leading eigenvectors of each thread
-  return (2 * (size_t)g.p * g.p + 2 * (size_t)g.p) * kstap::kFlipThreads * 8;
-}
-
-size_t smem_bfit(const Geom& g, bool from_store) {
-  const int P = g.p, PP = P * P, Q = g.q, TC = g.tc, R = g.r_b;
-  const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
-  size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
-  b += (size_t)TC * PP * 16;
-  // the eigen phase's basis scratch reuses the (then dead) lag and box-sum
-  // buffers; the lag store is read through two buffers (prefetch of the next lag)
-  const size_t vs = (size_t)(kstap::bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;
-  const size_t lagb = (from_store ? kstap::kLagStages : 1) * (size_t)PP * NUmax * 16 +
-                      (from_store ? 0 : 2 * (size_t)PP * WT * 16);
-  b += std::max(vs, lagb);
-  if (!from_store) b += (size_t)P * NR * WT * 8;
-  return b;
-}
-
-size_t smem_detect(const Geom& g) {
-  const int P = g.p, Q = g.q, V = g.V, R = g.r_b;
-  const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 4 * (size_t)P * R;
-  const size_t cells = cells_per_detect_block(Q);
-  const size_t QS = std::max(R, P + 1);   // near-blind queue entry (float2) per pair
-  return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8 +
-         (kstap::kThreads / 32) * kstap::kBlindQ * (QS * 8 + 4);
-}
-
-// Largest dynamic shared memory a CTA may opt into on sm_103a (227 KB).
-constexpr size_t kSmemOptin = 232448;
-
 // Checks every pass's shared-memory footprint for this geometry against the
 // per-CTA limit (the ring box and p set them).
 bool smem_fits(const Geom& g, bool lag_store, std::string& why) {
@@ -445,204 +333,24 @@ bool smem_fits(const Geom& g, bool lag_store, std::string& why) {
   return true;
 }
 
-// Persistent grid: SMs x resident CTAs x waves, capped by the tile count.
-template <typename K>
-int grid_for(K kernel, int threads, size_t smem, int tiles, int sm_count, int waves) {
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  const long cap = (long)sm_count * occ * std::max(1, waves);
-  return (int)std::max(1L, std::min<long>(tiles, cap));
-}
-
-// Frame scan of every job: max |component| (fixed-point scale) and the
-// non-finite flag, into each job's maxbits words (zeroed by the caller).
-kstap_status enqueue_scan(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                          int sm_count, cudaStream_t s) {
-  const size_t maxf = JL.table ? 0 : 2 * (size_t)g.p * JL.one.H_in * JL.one.W_in;
-  const int bx = JL.table ? sm_count * 2
-                          : (int)std::min<size_t>((maxf + 1023) / 1024, (size_t)sm_count * 16);
-  prof_collect(prof, KSTAP_K_SCALE);
-  prof_begin(prof, KSTAP_K_SCALE, s);
-  kstap::k_frame_maxabs<<<dim3(std::max(1, bx), JL.njobs), 256, 0, s>>>(g, JL);
-  prof_end(prof, KSTAP_K_SCALE, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
-  return KSTAP_OK;
-}
-
-// Enqueues the fit (scale, moments, flip-flop, B / U_B) of all jobs of JL.
-template <int P, int Q, int R>
-kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                         char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
-                         cudaStream_t s) {
-  float2* Mw = (float2*)(scratch + L.Mw);
-  float2* Sw = (float2*)(scratch + L.Sw);
-  float2* aw = (float2*)(scratch + L.aw);
-  float4* Lw = lag_store ? (float4*)(scratch + L.Lw) : nullptr;
-  if (JL.njobs < 1) return KSTAP_OK;
-  KSTAP_CUDA(ctx, cudaMemsetAsync(scratch + L.flags, 0, 8 * (size_t)JL.njobs, s));
-  kstap_status st = enqueue_scan(ctx, prof, g, JL, sm_count, s);
-  if (st != KSTAP_OK) return st;
-
-  const size_t sm1 = smem_moments(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_moments<P, Q>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-  const int g1 = grid_for(kstap::k_moments<P, Q>, kstap::kMomThreads, sm1,
-                          JL.ntiles[kstap::kKindMoments], sm_count, waves);
-  prof_collect(prof, KSTAP_K_MOMENTS);
-  prof_begin(prof, KSTAP_K_MOMENTS, s);
-  kstap::k_moments<P, Q><<<g1, kstap::kMomThreads, sm1, s>>>(g, JL, Mw, Sw, Lw);
-  prof_end(prof, KSTAP_K_MOMENTS, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
-
-  if constexpr (P <= 3) {
-    const int g2 = grid_for(kstap::k_flipflop<P>, 128, 0, JL.ntiles[kstap::kKindFlip], sm_count,
-                            waves);
-    prof_collect(prof, KSTAP_K_FLIPFLOP);
-    prof_begin(prof, KSTAP_K_FLIPFLOP, s);
-    kstap::k_flipflop<P><<<g2, 128, 0, s>>>(g, JL, Mw, Sw, aw);
-    prof_end(prof, KSTAP_K_FLIPFLOP, s);
-    KSTAP_CUDA(ctx, cudaGetLastError());
-  } else {
-    // stacked passes: M and the block sums from the lag store (a warp per
-    // cell), then Alg. 2 with a thread per cell
-    if (!lag_store) return fail(ctx, KSTAP_EINVAL, "p > 3 needs the lag store");
-    const size_t smg = smem_mgram(g);
-    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_mgram<P, Q>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
-    const int gm = grid_for(kstap::k_mgram<P, Q>, 64, smg, JL.ntiles[kstap::kKindMgram],
-                            sm_count, waves);
-    prof_collect(prof, KSTAP_K_MGRAM);
-    prof_begin(prof, KSTAP_K_MGRAM, s);
-    kstap::k_mgram<P, Q><<<gm, 64, smg, s>>>(g, JL, Mw, Sw, Lw);
-    prof_end(prof, KSTAP_K_MGRAM, s);
-    KSTAP_CUDA(ctx, cudaGetLastError());
-    const size_t smf = smem_flipt(g);
-    KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_flipflop_t<P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
-    const int gf = grid_for(kstap::k_flipflop_t<P>, kstap::kFlipThreads, smf,
-                            JL.ntiles[kstap::kKindFlip], sm_count, waves);
-    prof_collect(prof, KSTAP_K_FLIPFLOP);
-    prof_begin(prof, KSTAP_K_FLIPFLOP, s);
-    kstap::k_flipflop_t<P><<<gf, kstap::kFlipThreads, smf, s>>>(g, JL, Mw, Sw, aw);
-    prof_end(prof, KSTAP_K_FLIPFLOP, s);
-    KSTAP_CUDA(ctx, cudaGetLastError());
-  }
-
-  const size_t sm3 = smem_bfit(g, lag_store);
-  auto kb = kstap::k_bfit<P, Q, R, true>;
-  if constexpr (P <= 3) {
-    if (!lag_store) kb = kstap::k_bfit<P, Q, R, false>;
-  }
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-  constexpr int nt3 = kstap::bfit_threads(Q);
-  const int g3 = grid_for(kb, nt3, sm3, JL.ntiles[kstap::kKindBfit], sm_count, waves);
-  prof_collect(prof, KSTAP_K_BFIT);
-  prof_begin(prof, KSTAP_K_BFIT, s);
-  kb<<<g3, nt3, sm3, s>>>(g, JL, aw, Lw);
-  prof_end(prof, KSTAP_K_BFIT, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
-  return KSTAP_OK;
-}
-
-template <int P, int Q, int R, bool BF16>
-kstap_status enqueue_detect_tc(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                               int sm_count, int waves, cudaStream_t s) {
-  auto k = kstap::k_detect_tc<P, Q, R, BF16>;
-  const size_t sm = kstap::tc_smem_request(P, Q, R);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  constexpr int nt = kstap::tc_threads(Q);
-  const int grid = grid_for(k, nt, sm, JL.ntiles[kstap::kKindDetect], sm_count, waves);
-  prof_collect(prof, KSTAP_K_DETECT);
-  prof_begin(prof, KSTAP_K_DETECT, s);
-  k<<<grid, nt, sm, s>>>(g, JL, ctx->bank_op, ctx->bank_inv, ctx->bank_aT, ctx->bank_bT,
-                         ctx->bank_n2);
-  prof_end(prof, KSTAP_K_DETECT, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
-  return KSTAP_OK;
-}
-
-template <int P, int Q, int R, int RA>
-kstap_status enqueue_detect_fp32(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                                 int sm_count, int waves, cudaStream_t s);
-
-template <int P, int Q, int R>
-kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                            int sm_count, int waves, cudaStream_t s) {
-  if (JL.njobs < 1) return KSTAP_OK;
-  if (g.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
-  if constexpr (P <= 3) {
-    if (ctx->prm.precision == KSTAP_FP16X3)
-      return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
-    if (ctx->prm.precision == KSTAP_BF16X3)
-      return enqueue_detect_tc<P, Q, R, true>(ctx, prof, g, JL, sm_count, waves, s);
-  }
-  return enqueue_detect_fp32<P, Q, R, 1>(ctx, prof, g, JL, sm_count, waves, s);
-}
-
-template <int P, int Q, int R, int RA>
-kstap_status enqueue_detect_fp32(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
-                                 int sm_count, int waves, cudaStream_t s) {
-  const size_t sm = smem_detect(g);
-  KSTAP_CUDA(ctx, cudaFuncSetAttribute(kstap::k_detect<P, Q, R, RA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const int grid = grid_for(kstap::k_detect<P, Q, R, RA>, kstap::kThreads, sm,
-                            JL.ntiles[kstap::kKindDetect], sm_count, waves);
-  prof_collect(prof, KSTAP_K_DETECT);
-  prof_begin(prof, KSTAP_K_DETECT, s);
-  kstap::k_detect<P, Q, R, RA><<<grid, kstap::kThreads, sm, s>>>(g, JL, ctx->bank_aT,
-                                                                   ctx->bank_bT, ctx->bank_n2);
-  prof_end(prof, KSTAP_K_DETECT, s);
-  KSTAP_CUDA(ctx, cudaGetLastError());
-  return KSTAP_OK;
-}
-
-#define KSTAP_DISPATCH(QQ, RR, CALL) \
-  if (g.q == QQ && g.r_b == RR) return CALL;
-#define KSTAP_DISPATCH_ALL(CALLT)                                         \
-  KSTAP_DISPATCH(8, 1, CALLT(8, 1)) KSTAP_DISPATCH(8, 2, CALLT(8, 2))     \
-  KSTAP_DISPATCH(8, 3, CALLT(8, 3)) KSTAP_DISPATCH(8, 4, CALLT(8, 4))     \
-  KSTAP_DISPATCH(16, 1, CALLT(16, 1)) KSTAP_DISPATCH(16, 2, CALLT(16, 2)) \
-  KSTAP_DISPATCH(16, 3, CALLT(16, 3)) KSTAP_DISPATCH(16, 4, CALLT(16, 4)) \
-  KSTAP_DISPATCH(32, 1, CALLT(32, 1)) KSTAP_DISPATCH(32, 2, CALLT(32, 2)) \
-  KSTAP_DISPATCH(32, 3, CALLT(32, 3)) KSTAP_DISPATCH(32, 4, CALLT(32, 4))
-
-#define KSTAP_DISPATCH_P6(CALLT)                                          \
-  KSTAP_DISPATCH(8, 1, CALLT(8, 1)) KSTAP_DISPATCH(8, 2, CALLT(8, 2))     \
-  KSTAP_DISPATCH(8, 3, CALLT(8, 3)) KSTAP_DISPATCH(8, 4, CALLT(8, 4))     \
-  KSTAP_DISPATCH(16, 1, CALLT(16, 1)) KSTAP_DISPATCH(16, 2, CALLT(16, 2)) \
-  KSTAP_DISPATCH(16, 3, CALLT(16, 3)) KSTAP_DISPATCH(16, 4, CALLT(16, 4))
-
 kstap_status dispatch_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                           char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
                           cudaStream_t s) {
-  if (g.p == 6) {
-#define KSTAP_FIT6(QQ, RR) \
-  enqueue_fit<6, QQ, RR>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s)
-    KSTAP_DISPATCH_P6(KSTAP_FIT6)
-#undef KSTAP_FIT6
-    return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b) for p = 6");
-  }
-#define KSTAP_FITC(QQ, RR) \
-  enqueue_fit<3, QQ, RR>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s)
-  KSTAP_DISPATCH_ALL(KSTAP_FITC)
-#undef KSTAP_FITC
-  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
+#define KSTAP_FIT_CLASS(P, Q) \
+  if (g.p == P && g.q == Q) return fit_##P##_##Q(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);
+  KSTAP_CLASSES(KSTAP_FIT_CLASS)
+#undef KSTAP_FIT_CLASS
+  return fail(ctx, KSTAP_EINVAL, "unsupported (p, q) = (%d, %d)", g.p, g.q);
 }
 
 kstap_status dispatch_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                              int sm_count, int waves, cudaStream_t s) {
-  if (g.p == 6) {
-#define KSTAP_DET6(QQ, RR) enqueue_detect<6, QQ, RR>(ctx, prof, g, JL, sm_count, waves, s)
-    KSTAP_DISPATCH_P6(KSTAP_DET6)
-#undef KSTAP_DET6
-    return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b) for p = 6");
-  }
-#define KSTAP_DETC(QQ, RR) enqueue_detect<3, QQ, RR>(ctx, prof, g, JL, sm_count, waves, s)
-  KSTAP_DISPATCH_ALL(KSTAP_DETC)
-#undef KSTAP_DETC
-  return fail(ctx, KSTAP_EINVAL, "unsupported (q, r_b)");
+  if (JL.njobs < 1) return KSTAP_OK;
+#define KSTAP_DETECT_CLASS(P, Q) \
+  if (g.p == P && g.q == Q) return detect_##P##_##Q(ctx, prof, g, JL, sm_count, waves, s);
+  KSTAP_CLASSES(KSTAP_DETECT_CLASS)
+#undef KSTAP_DETECT_CLASS
+  return fail(ctx, KSTAP_EINVAL, "unsupported (p, q) = (%d, %d)", g.p, g.q);
 }
 
 kstap_status check_frame(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in) {
@@ -782,6 +490,7 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
   e = cudaMalloc(&ctx->report, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) {
     ctx->det_flags = (unsigned*)(ctx->report + 2);
+    ctx->fault = (unsigned*)(ctx->report + 3);
     e = cudaMemset(ctx->report, 0, 4 * sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_aT, aT.size() * sizeof(float2));
@@ -1169,10 +878,13 @@ kstap_status kstap_destroy(kstap_ctx* ctx) {
 kstap_status kstap_device_status(kstap_ctx* ctx) {
   if (!ctx) return KSTAP_EINVAL;
   KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  unsigned f = 0, z = 0;
-  KSTAP_CUDA(ctx, cudaMemcpyFromSymbol(&f, kstap::g_fault, sizeof(f)));
+  unsigned f = 0;
+  KSTAP_CUDA(ctx, cudaMemcpy(&f, ctx->fault, sizeof(f), cudaMemcpyDeviceToHost));
   if (f) {
-    KSTAP_CUDA(ctx, cudaMemcpyToSymbol(kstap::g_fault, &z, sizeof(z)));
+    KSTAP_CUDA(ctx, cudaMemset(ctx->fault, 0, sizeof(f)));
+    if (f & 2u)
+      return fail(ctx, KSTAP_ECUDA, "a tensor-core completion never arrived and the tile's tensor "
+                  "memory was freed (fault word 0x%x): the device state is unknown", f);
     return fail(ctx, KSTAP_ECUDA, "a tensor-core completion wait gave up (fault word 0x%x)", f);
   }
   return KSTAP_OK;
@@ -1358,7 +1070,7 @@ void launch_batch(Server* s, const std::vector<std::pair<uint64_t, int>>& items)
   if (status != KSTAP_OK) {
     std::lock_guard<std::mutex> lock(s->mu);
     for (auto& it : items) s->reqs[it.first].state = 3;
-    s->err = ctx->err;
+    s->err = t_err_sink ? *t_err_sink : std::string("batch launch failed");
   }
   if (cudaLaunchHostFunc(st, batch_done, b) != cudaSuccess) {
     // could not register the completion callback: finish synchronously
@@ -1369,6 +1081,8 @@ void launch_batch(Server* s, const std::vector<std::pair<uint64_t, int>>& items)
 
 void worker_loop(Server* s) {
   cudaSetDevice(s->device);
+  std::string worker_err;
+  t_err_sink = &worker_err;
   std::unique_lock<std::mutex> lock(s->mu);
   auto part_bytes = [&](const std::pair<uint64_t, int>& it) {
     return s->reqs[it.first].parts[it.second].scratch_bytes;
@@ -1569,7 +1283,11 @@ kstap_status kstap_poll(kstap_ctx* ctx, uint64_t ticket, kstap_result* out, int 
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return fail(ctx, KSTAP_ENOTFOUND, "unknown ticket %llu",
                                        (unsigned long long)ticket);
-  auto ready = [&] { return s->reqs[ticket].state >= 2; };
+  // a ticket released by another thread while this one waits counts as done
+  auto ready = [&] {
+    auto f = s->reqs.find(ticket);
+    return f == s->reqs.end() || f->second.state >= 2;
+  };
   if (!ready()) {
     if (timeout_us == 0) return KSTAP_EAGAIN;
     if (timeout_us < 0)
@@ -1577,7 +1295,11 @@ kstap_status kstap_poll(kstap_ctx* ctx, uint64_t ticket, kstap_result* out, int 
     else if (!s->cv.wait_for(lock, std::chrono::microseconds(timeout_us), ready))
       return KSTAP_ETIMEOUT;
   }
-  const Server::Req& r = s->reqs[ticket];
+  it = s->reqs.find(ticket);
+  if (it == s->reqs.end())
+    return fail(ctx, KSTAP_ENOTFOUND, "ticket %llu was released while waiting",
+                (unsigned long long)ticket);
+  const Server::Req& r = it->second;
   if (r.state == 3) return fail(ctx, KSTAP_ECUDA, "request failed: %s", s->err.c_str());
   out->ticket = ticket;
   out->H = r.H;
@@ -1617,9 +1339,11 @@ kstap_status kstap_release(kstap_ctx* ctx, uint64_t ticket) {
 // scale word and the per-cell moments M, block sums and flip-flop factor a --
 // lives in this file-scope device array instead of a cudaMalloc'd workspace.
 // Host code must not pass the array's name to a kernel: on the host it is only
-// a stand-in symbol.  The device address is looked up once per device with
-// cudaGetSymbolAddress and cached.  The B pass recomputes the lag sums (no lag
-// store), which keeps the array at ~16.5 MB.
+// a stand-in symbol.  The device address is looked up with
+// cudaGetSymbolAddress on the current device at every call (no caching, so a
+// context torn down and recreated by cudaDeviceReset is picked up).  The B
+// pass recomputes the lag sums (no lag store), which keeps the array at
+// ~16.5 MB.
 // ---------------------------------------------------------------------------
 #define KSTAP_NOALLOC_MAX_CELLS 32768
 #define KSTAP_NOALLOC_SCRATCH_BYTES (256 + (size_t)KSTAP_NOALLOC_MAX_CELLS * (45 + 9 + 9) * 8 + 1024)
@@ -1628,29 +1352,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[KSTAP_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device (looked up on
-// the first call per device).
+// Device address of g_noalloc_scratch on the current device.
 kstap_status noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess)
-    return fail(nullptr, KSTAP_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices)
-    return fail(nullptr, KSTAP_EINVAL, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(nullptr, KSTAP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
-                  cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(nullptr, KSTAP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
+                cudaGetErrorString(e));
+  *out = p;
   return KSTAP_OK;
 }
 

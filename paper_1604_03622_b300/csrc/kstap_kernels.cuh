@@ -189,38 +189,6 @@ __host__ __device__ constexpr int tri_idx(int n, int J, int Jp) {
   return J * n - (J * (J - 1)) / 2 + (Jp - J);
 }
 
-// ------------------------------------------------------- frame scale -------
-// max |component| of Y via the order-preserving bit pattern of non-negative
-// floats; non-finite values are recorded in *nonfinite.
-__global__ void k_frame_maxabs(Geom g0, JobList L) {
-  const Job& J = L.table ? L.table[blockIdx.y] : L.one;
-  const float* __restrict__ Y = reinterpret_cast<const float*>(J.Y);
-  const size_t plane = 2 * (size_t)J.H_in * J.W_in;   // floats of one channel of this job
-  const size_t nfloat = plane * g0.p;
-  unsigned* maxbits = J.maxbits;
-  unsigned* nonfinite = J.maxbits + 1;
-  unsigned m = 0, bad = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nfloat;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t ch = i / plane;
-    const float a = fabsf(__ldg(Y + ch * 2 * (size_t)J.ch_stride + (i - ch * plane)));
-    if (a <= kFltMax) {
-      m = max(m, __float_as_uint(a));
-    } else {
-      bad = 1;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(maxbits, m);
-    if (bad) atomicOr(nonfinite, 1u);
-  }
-}
-
 // ------------------------------------------------ shared lag-sum stage -----
 // Loads the fixed-point tile of rows [r, r + 2Rr] and columns [c0, c0 + WT)
 // of all channels: Yq[(i * NR + rho) * WT + col].

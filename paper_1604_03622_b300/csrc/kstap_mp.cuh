@@ -5,9 +5,7 @@
 // a warp per strip of cells with sliding windows, and k_flipflop_t runs
 // Alg. 2 with a thread per cell, streaming M from the per-cell arrays.
 // The B / U_B pass (k_bfit) and the projection (k_detect) are the
-// single-pass kernels instantiated for more channels.  k_change forms the
-// per-pass maxima of the statistic and their difference (the noncoherent
-// change detection of Sec. 8).
+// single-pass kernels instantiated for more channels.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -415,26 +413,6 @@ k_flipflop_t(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* _
     JB.eta[local] = bad ? __int_as_float(0x7fc00000) : (float)sqrt(e2 > 0.0 ? e2 : 0.0);
   }
   }  // tile loop
-}
-
-// Per cell: Tmax_k = max over the V velocities of pass k of T_all (K V per
-// cell, pass-major), and change = Tmax_{K-1} - Tmax_0 (mission minus
-// reference pixel magnitude after filtering).
-__global__ void k_change(const float* __restrict__ T_all, long long ncell, int V, int K,
-                         float* __restrict__ Tmax_k, float* __restrict__ change) {
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const float* t = T_all + c * (long long)K * V;
-    float first = 0.f, last = 0.f;
-    for (int k = 0; k < K; ++k) {
-      float m = t[(size_t)k * V];
-      for (int v = 1; v < V; ++v) m = fmaxf(m, t[(size_t)k * V + v]);
-      if (Tmax_k) Tmax_k[(size_t)k * ncell + c] = m;
-      if (k == 0) first = m;
-      last = m;
-    }
-    if (change) change[c] = last - first;
-  }
 }
 
 }  // namespace kstap

@@ -27,9 +27,6 @@
 
 namespace kstap {
 
-// Device-wide fault word: bit 0 = a tensor-core completion wait gave up.
-__device__ unsigned g_fault;
-
 constexpr int kTcCells = 16;        // cells per tile
 constexpr int kTcRowsPerCell = 16;  // operand rows per cell: 2 (p + r_b) <= 16 used
 constexpr int kTcN = kTcCells * kTcRowsPerCell;   // 256 = MMA N
@@ -148,12 +145,15 @@ __host__ __device__ constexpr size_t tc_smem_request(int P, int Q, int R) {
 
 // CTA = tc_threads(Q) threads; tiles of kTcCells cells over all jobs.
 // bank_op: the bank operand image (hi block then lo block, tc_off layout),
-// bank_inv = 1 / (power-of-two bank scale).
+// bank_inv = 1 / (power-of-two bank scale).  fault: a device word the host
+// reads back; bit 0 = a completion wait gave up (the launch's results are
+// not valid), bit 1 = the MMAs had still not completed when the CTA freed
+// its tensor memory (the device's state is unknown).
 template <int P, int Q, int R, bool BF16>
 __global__ void __launch_bounds__(tc_threads(Q), tc_threads(Q) >= 512 ? 1 : 2)
 k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_inv,
             const float2* __restrict__ bank_aT, const float2* __restrict__ bank_bT,
-            const float* __restrict__ bank_n2) {
+            const float* __restrict__ bank_n2, unsigned* __restrict__ fault) {
   constexpr int NT = tc_threads(Q);
   constexpr int G = Q;                       // lanes per cell in the projection phase
   constexpr int K2 = 2 * Q;                  // real contraction length
@@ -364,14 +364,18 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
     }
     bool ok = mbar_wait(smem_u32(&mbar), phase);
     if (!ok) {
-      atomicOr(&g_fault, 1u);
-      ok = mbar_wait(smem_u32(&mbar), phase);   // let the MMAs drain before leaving
+      atomicOr(fault, 1u);
+      ok = mbar_wait(smem_u32(&mbar), phase);   // the MMAs may still complete
     }
-    phase ^= 1u;
     if (__syncthreads_or(!ok)) {
+      // the tile is abandoned; the tensor memory is freed below, so the MMAs
+      // get one last bounded wait first, and a commit that never arrives is
+      // reported as an unknown device state
+      if (!ok && !mbar_wait(smem_u32(&mbar), phase)) atomicOr(fault, 2u);
       abort = true;
       break;
     }
+    phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
     // ---- epilogue: thread = velocity v, cells of its set
