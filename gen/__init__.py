@@ -20,7 +20,11 @@ Data model (Sec. 2 of the paper, SIRV clutter model, texture tau = 1):
     e_k[j] = exp(j 2 pi nu_k j).
   * Clutter tones nu_k are spaced 1.25 / q cycles/sample apart (+-10% jitter,
     common offset U(-0.02, 0.02)), so the r_b temporal clutter directions are
-    resolvable inside one q-window.
+    resolvable inside one q-window.  With tone_band = w (make_frame) they are
+    instead drawn independently and uniformly in [-w, w] cycles/sample (w =
+    0.05: the narrow clutter band of a slow platform); tones closer than a
+    Doppler bin make the trailing clutter eigenvalues of B small, so the
+    eigengap of B at rank r_b spans many decades over the cells of a frame.
   * A_ij = 0.9^|i-j| exp(j phi (i-j)), one phi ~ U(-pi, pi) per frame: a
     modulated AR(1) covariance, Hermitian Toeplitz and positive definite.
   * Noise is CN(0, sigma^2) per pixel and channel, sigma^2 = 1.
@@ -156,8 +160,13 @@ def steering_bank(p: int, q: int, V: int) -> Tuple[np.ndarray, np.ndarray]:
     return a.astype(np.complex64), b.astype(np.complex64)
 
 
-def clutter_tones(q: int, r_b: int, rng: np.random.Generator) -> Tuple[np.ndarray, float]:
-    """Clutter tones (cycles/sample) 1.25 bins apart, and the band half-width."""
+def clutter_tones(q: int, r_b: int, rng: np.random.Generator,
+                  band: Optional[float] = None) -> Tuple[np.ndarray, float]:
+    """Clutter tones (cycles/sample) 1.25 bins apart -- or, with `band`, drawn
+    uniformly in [-band, band] -- and the band half-width."""
+    if band is not None:
+        nu = np.sort(rng.uniform(-band, band, size=r_b))
+        return nu, float(band)
     s = 1.25 / q
     off = rng.uniform(-0.02, 0.02)
     jit = rng.uniform(-0.1 * s, 0.1 * s, size=r_b)
@@ -187,7 +196,7 @@ def _cn(rng: np.random.Generator, shape, dtype=np.float64) -> np.ndarray:
 
 def make_frame(wl: Workload, seed: Optional[int] = None, clutter: bool = True,
                noise: bool = True, targets: bool = True, texture_nu: Optional[float] = None,
-               training_targets: int = 0) -> Frame:
+               training_targets: int = 0, tone_band: Optional[float] = None) -> Frame:
     """Draw one seeded frame for workload `wl` (see the module docstring)."""
     seed = wl.seed if seed is None else seed
     p, q, H_in, W_in = wl.p, wl.q, wl.H_in, wl.W_in
@@ -197,7 +206,7 @@ def make_frame(wl: Workload, seed: Optional[int] = None, clutter: bool = True,
     phi = rng_c.uniform(-np.pi, np.pi)
     A = spatial_cov(p, phi)
     L_A = np.linalg.cholesky(A)
-    tones, band = clutter_tones(q, wl.r_b, rng_c)
+    tones, band = clutter_tones(q, wl.r_b, rng_c, tone_band)
     w = 2.0 ** -np.arange(wl.r_b)
     mus = wl.sigma2 * 10 ** (wl.cnr_db / 10.0) * w / w.sum()
     g = _cn(rng_c, (wl.r_b, H_in, p))                              # g_k(row)
@@ -333,7 +342,8 @@ class MultipassFrame:
 
 
 def make_multipass_frame(wl: Workload, K: int = 2, coherence: float = 0.9,
-                         seed: Optional[int] = None) -> MultipassFrame:
+                         seed: Optional[int] = None,
+                         tone_band: Optional[float] = None) -> MultipassFrame:
     """K registered passes over the same scene (Sec. 3), stacked as K p channels.
 
     The clutter of pass k is A_k^{1/2} g_k(row) exp(j 2 pi nu col) per tone,
@@ -349,7 +359,7 @@ def make_multipass_frame(wl: Workload, K: int = 2, coherence: float = 0.9,
     p, q, H_in, W_in = wl.p, wl.q, wl.H_in, wl.W_in
     Y = np.zeros((K * p, H_in, W_in), dtype=np.complex64)
     rng_c = np.random.default_rng([seed, STREAM_CLUTTER])
-    tones, band = clutter_tones(q, wl.r_b, rng_c)
+    tones, band = clutter_tones(q, wl.r_b, rng_c, tone_band)
     w = 2.0 ** -np.arange(wl.r_b)
     mus = wl.sigma2 * 10 ** (wl.cnr_db / 10.0) * w / w.sum()
     g0 = _cn(rng_c, (wl.r_b, H_in))

@@ -144,11 +144,18 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
                                const kstap_factors* factors);
 
 /* Waits for the context stream, then reports the last kstap_fit_project or
- * kstap_run_batch: cells whose Alg. 2 loop stopped at max_iter and cells
- * flagged for non-finite input (either pointer may be NULL).  Returns
- * KSTAP_WARN_NOCONV if any cell stopped at max_iter (its factors are the last
- * iterate, valid but not converged to eps), else KSTAP_OK. */
-kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite);
+ * kstap_run_batch: cells whose Alg. 2 loop stopped at max_iter, cells flagged
+ * for non-finite input, and cells whose EIG_{r_b} (Sec. 4) took the
+ * ill-gapped path: their leading r_b eigenvalues of B were not separated
+ * from the next one well enough for subspace iteration on r_b vectors (the
+ * rate estimate left more than ~2e-7 of subspace error after 4 steps), so
+ * U_B and lambda_B were recomputed by block subspace iteration on min(q, 8)
+ * vectors with a Rayleigh-Ritz step solved by FP64 Jacobi sweeps.  Any
+ * pointer may be NULL.  Returns KSTAP_WARN_NOCONV if any cell stopped at
+ * max_iter (its factors are the last iterate, valid but not converged to
+ * eps), else KSTAP_OK. */
+kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite,
+                              long long* eig_refined);
 
 /* Steps 3-4 above (Eq. KronSTAP and the velocity bank) with the factors of a
  * previous kstap_fit_project on the same frame.  Outputs (device, H * W):

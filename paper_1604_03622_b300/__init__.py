@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_double), P]
         L.kstap_change_map.argtypes = [P, ctypes.c_longlong, I, I, P, P, P]
         L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
@@ -165,13 +166,14 @@ def kstap_fit_project(ctx: int, Y, H_in: int, W_in: int, factors: KstapFactors) 
 
 
 def kstap_fit_report(ctx: int):
-    """(nonconverged, nonfinite) cell counts of the last fit; waits for the stream.
-    A KSTAP_WARN_NOCONV status is returned in the counts, not raised."""
-    nc, nf = ctypes.c_longlong(), ctypes.c_longlong()
-    st = lib().kstap_fit_report(ctx, ctypes.byref(nc), ctypes.byref(nf))
+    """(nonconverged, nonfinite, eig_refined) cell counts of the last fit; waits
+    for the stream.  A KSTAP_WARN_NOCONV status is returned in the counts, not
+    raised."""
+    nc, nf, nr = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib().kstap_fit_report(ctx, ctypes.byref(nc), ctypes.byref(nf), ctypes.byref(nr))
     if st != KSTAP_WARN_NOCONV:
         _check(st, ctx)
-    return int(nc.value), int(nf.value)
+    return int(nc.value), int(nf.value), int(nr.value)
 
 
 def kstap_lrkron_fit(X, r_a: int = 1, eps: float = 1e-6, max_iter: int = 100, A_out=None,

@@ -487,11 +487,11 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
     n2[v] = (float)sa;
     n2[V + v] = (float)sb;
   }
-  e = cudaMalloc(&ctx->report, 4 * sizeof(unsigned long long));
+  e = cudaMalloc(&ctx->report, kReportWords * sizeof(unsigned long long));
   if (e == cudaSuccess) {
-    ctx->det_flags = (unsigned*)(ctx->report + 2);
-    ctx->fault = (unsigned*)(ctx->report + 3);
-    e = cudaMemset(ctx->report, 0, 4 * sizeof(unsigned long long));
+    ctx->det_flags = (unsigned*)(ctx->report + 4);
+    ctx->fault = (unsigned*)(ctx->report + 5);
+    e = cudaMemset(ctx->report, 0, kReportWords * sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_aT, aT.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->bank_bT, bT.size() * sizeof(float2));
@@ -576,7 +576,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
   }
   const std::vector<Frame> strips = (rows >= H) ? std::vector<Frame>{whole}
                                                 : split_rows(p, ctx->V, whole, rows);
-  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, kReportCounters * sizeof(unsigned long long), ctx->stream));
   for (const Frame& s : strips) {
     const int sh = s.H_in - 2 * p.ring_r;
     const Layout L = make_layout(p, {{sh, W}}, true);
@@ -645,17 +645,19 @@ kstap_status kstap_run_batch(kstap_ctx* ctx, const kstap_frame* frames, int n) {
     KSTAP_CUDA(ctx, cudaMemcpyAsync(ctx->jobs_dev, host.data(), n * sizeof(Job),
                                     cudaMemcpyHostToDevice, ctx->stream));
   }
-  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, kReportCounters * sizeof(unsigned long long), ctx->stream));
   return enqueue_batch(ctx, ctx, fr, L, (char*)ctx->ws, ctx->jobs_dev, ctx->stream, ctx->report);
 }
 
-kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite) {
+kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite,
+                              long long* eig_refined) {
   if (!ctx) return KSTAP_EINVAL;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   KSTAP_CUDA(ctx, cudaMemcpyAsync(h, ctx->report, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   KSTAP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (nonconverged) *nonconverged = (long long)h[0];
   if (nonfinite) *nonfinite = (long long)h[1];
+  if (eig_refined) *eig_refined = (long long)h[2];
   return h[0] ? KSTAP_WARN_NOCONV : KSTAP_OK;
 }
 

@@ -60,8 +60,10 @@ struct kstap_ctx {
   int kernel_launches[kstap_nkernels] = {};
   bool ev_pending[kstap_nkernels] = {};
   struct Server* server = nullptr;   // created by the first kstap_submit
-  // device words: frame scan of kstap_detect (max bits, non-finite flag) and
-  // the counters of the last fit ([0] cells at max_iter, [1] non-finite cells)
+  // device words (kReportWords): the counters of the last fit ([0] cells at
+  // max_iter, [1] non-finite cells, [2] cells whose B eigenspace was
+  // recomputed by the ill-gapped path), then the frame scan of kstap_detect
+  // (max bits, non-finite flag) and the tensor-core fault word
   unsigned* det_flags = nullptr;
   unsigned long long* report = nullptr;
   // device word of the tensor-core detect (bit 0: a completion wait gave up,
@@ -77,6 +79,9 @@ struct kstap_graph {
 };
 
 namespace kh {
+
+constexpr int kReportCounters = 3;   // fit counters at the start of kstap_ctx::report
+constexpr int kReportWords = 8;
 
 // Records the message as ctx's last error (or, for ctx == NULL, as the
 // calling thread's last context-free error) and returns st.
@@ -147,17 +152,10 @@ inline size_t smem_flipt(const Geom& g) {
 
 inline size_t smem_bfit(const Geom& g, bool from_store) {
   const int P = g.p, PP = P * P, Q = g.q, TC = g.tc, R = g.r_b;
-  const int NR = 2 * g.Rr + 1, WT = TC + 2 * g.Ra + Q - 1, NUmax = TC + Q - 1;
-  size_t b = (size_t)TC * (Q * (Q + 1) / 2) * 16;
-  b += (size_t)TC * PP * 16;
-  // the eigen phase's basis scratch reuses the (then dead) lag and box-sum
-  // buffers; the lag store is read through two buffers (prefetch of the next lag)
-  const size_t vs = (size_t)(kstap::bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;
-  const size_t lagb = (from_store ? kstap::kLagStages : 1) * (size_t)PP * NUmax * 16 +
-                      (from_store ? 0 : 2 * (size_t)PP * WT * 16);
-  b += std::max(vs, lagb);
-  if (!from_store) b += (size_t)P * NR * WT * 8;
-  return b;
+  // the tile's B (float-float upper triangles) and a, then the lag / basis /
+  // ill-gapped-cell region (kstap::bfit_region_bytes, shared with the kernel)
+  return (size_t)TC * (Q * (Q + 1) / 2) * 16 + (size_t)TC * PP * 16 +
+         (size_t)kstap::bfit_region_bytes(P, Q, R, TC, g.Ra, g.Rr, from_store);
 }
 
 inline size_t smem_detect(const Geom& g) {

@@ -90,7 +90,8 @@ struct JobList {
   int njobs;
   int ntiles[kKinds];
   long long NC;                 // total cells (stride of the per-cell workspace arrays)
-  unsigned long long* report;   // optional counters: [0] cells at max_iter, [1] cells flagged non-finite
+  unsigned long long* report;   // optional counters: [0] cells at max_iter, [1] cells flagged
+                                // non-finite, [2] cells of the ill-gapped EIG_{r_b} path
 };
 
 __device__ __forceinline__ const Job& job_of(const JobList& L, int kind, int tile, int& local) {
@@ -743,6 +744,17 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
           if (m < ra) s = cadd(s, cscale(cmul(U[i][m], cconj(U[k][m])), d[m]));
         an_new[i + P * k] = s;
       }
+    // exactly Hermitian (the two roundings of u_i conj(u_k) and u_k conj(u_i)
+    // differ): the B pass forms only the upper triangle of B = sum_J
+    // conj(a_J) L_J and mirrors it, which equals the Hermitian part of b only
+    // for a Hermitian a; the anti-Hermitian rounding residue would move the
+    // ill-gapped eigenvectors of B by ~1e-7 lambda_1 / gap
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      an_new[i + P * i].y = 0.f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) an_new[i + P * k] = cconj(an_new[k + P * i]);
+    }
 #pragma unroll
     for (int J = 0; J < PP; ++J) {
       dn += cabs2(csub(an_new[J], a[J]));
@@ -889,18 +901,86 @@ __device__ __forceinline__ void orthonormalise_g(float2 (&x)[R]) {
   }
 }
 
+// Ritz values of a subspace step: the eigenvalues of the Hermitian part of
+// the R x R matrix H = V^H B V (FP32), in decreasing order.
+template <int R>
+__device__ __forceinline__ void ritz_values(const float2 (&H)[R][R], float (&lam)[R]) {
+  {
+    float2 Hh[R][R];   // Hermitian part of V^H B V (the Jacobi below assumes it)
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+      for (int mp = 0; mp < R; ++mp)
+        Hh[m][mp] = make_float2(0.5f * (H[m][mp].x + H[mp][m].x), 0.5f * (H[m][mp].y - H[mp][m].y));
+    if constexpr (R == 1) {
+      lam[0] = Hh[0][0].x;
+    } else if constexpr (R == 2) {
+      // the larger root directly, the smaller as det / larger (no cancellation)
+      const float a = Hh[0][0].x, d = Hh[1][1].x, h = 0.5f * (a - d), m = 0.5f * (a + d);
+      const float r = sqrtf(h * h + cabs2(Hh[0][1]));
+      const float det = a * d - cabs2(Hh[0][1]);
+      lam[0] = m + r;
+      lam[1] = (m + r != 0.f) ? det / (m + r) : m - r;
+    } else if constexpr (R == 3) {
+      // closed form (trigonometric solution of the characteristic cubic of
+      // the shifted, scaled matrix (H - q I) / p, q = tr H / 3): the three
+      // Ritz values are well separated relative to the largest here, so its
+      // single-precision rounding is far inside the tolerance of lambda_B
+      const float a11 = Hh[0][0].x, a22 = Hh[1][1].x, a33 = Hh[2][2].x;
+      const float2 a12 = Hh[0][1], a13 = Hh[0][2], a23 = Hh[1][2];
+      const float q = (a11 + a22 + a33) * (1.f / 3.f);
+      const float b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
+      const float s12 = cabs2(a12), s13 = cabs2(a13), s23 = cabs2(a23);
+      const float p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (s12 + s13 + s23);
+      if (!(p2 > 0.f)) {
+        lam[0] = lam[1] = lam[2] = q;
+      } else {
+        const float p = sqrtf(p2 * (1.f / 6.f));
+        const float2 t = cmul(a12, a23);
+        const float det = b11 * b22 * b33 + 2.f * (t.x * a13.x + t.y * a13.y) - b11 * s23 -
+                          b22 * s13 - b33 * s12;   // det(H - q I)
+        const float r = fminf(1.f, fmaxf(-1.f, det / (2.f * p * p * p)));
+        const float phi = acosf(r) * (1.f / 3.f);
+        const float l1 = q + 2.f * p * cosf(phi);
+        const float l3 = q + 2.f * p * cosf(phi + 2.0943951f);   // + 2 pi / 3
+        lam[0] = l1;
+        lam[1] = 3.f * q - l1 - l3;
+        lam[2] = l3;
+      }
+    } else {
+      float dd[R];
+      float2 UU[R][R];
+      // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
+      // by ~1e-10 lambda_1^2 / gap
+      jacobi_small<R, false>(Hh, dd, UU, 1e-10f);
+#pragma unroll
+      for (int m = 0; m < R; ++m) lam[m] = dd[m];
+    }
+  }
+}
+
+constexpr float kSubTol = 1e-8f;   // accepted error of the leading subspace of B
+constexpr int kSubSteps = 4;       // float-float subspace steps before a cell is handed on
+
 // Leading R-dimensional eigenspace of one cell's B (group of Q lanes, lane j
 // = row j).  Start: R columns of B (they lie mostly in the clutter subspace),
 // orthonormalised; one FP32 subspace step on B_hi; then float-float subspace
-// steps Y = B V with Cholesky-QR, U = Y L^-H.  Each float-float step measures
-// how far it moved the subspace, |U - V V^H U|_F = |(Y - V H) L^-H|_F with
-// H = V^H Y (also the Ritz matrix), and the loop stops once that change is
-// below 1e-6 (the next step would move it by a further factor
-// lambda_{R+1} / lambda_R).  The Ritz values are the eigenvalues of the last
-// V^H B V.  Loop exits are warp-uniform because several cells share a warp;
-// `live` = this group's cell exists (dead groups compute on zeros).
+// steps Y = B V with Cholesky-QR, U = Y L^-H.  Each step measures how far it
+// moved the subspace, c_k = |U - V V^H U|_F = |(Y - V H) L^-H|_F with
+// H = V^H Y (the Ritz matrix of V).  Subspace iteration contracts the error
+// by rho = lambda_{R+1} / lambda_R per step; an upper bound is
+// (tr B - sum of the Ritz values) / (smallest Ritz value), since the
+// remaining trace bounds lambda_{R+1} and Ritz values never exceed the
+// eigenvalues.  The error left after step k is then at most about
+// c_k rho / (1 - rho), and the loop stops once that is below kSubTol.
+// Returns false if it is not after kSubSteps steps (an ill-gapped cell:
+// lambda_{R+1} close to lambda_R, e.g. clutter tones closer than a Doppler
+// bin), whose subspace the caller recomputes with eig_block_rr.  lam = the
+// Ritz values of the last step.  Loop exits are warp-uniform because several
+// cells share a warp; `live` = this group's cell exists (dead groups compute
+// on zeros).
 template <int Q, int R>
-__device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live,
+__device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live,
                                  float2* __restrict__ Vs, float2 (&uh)[R], float2 (&ul)[R],
                                  float (&lam)[R]) {
   float2 v[R], y[R];
@@ -919,12 +999,15 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   // measure of the float-float step below relies on (a one-pass Cholesky-QR
   // of the unnormalised start would leave ~eps cond^2)
   orthonormalise_g<Q, R>(y);
+  // tr B (for the bound on lambda_{R+1})
+  const float trB = grp_sum<Q>(b_at<Q>(Bc, j, j).x);
 #pragma unroll
   for (int m = 0; m < R; ++m) v[m] = y[m];
 
   cff U[R];
   float2 H[R][R];
-  for (int step = 0; step < 4; ++step) {
+  bool converged = !live;
+  for (int step = 0; step < kSubSteps; ++step) {
 #pragma unroll
     for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
     __syncwarp();
@@ -1017,72 +1100,392 @@ __device__ void eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     const float change = grp_sum<Q>(local);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
-    const bool done = !live || change < 1e-12f;
-    if (__all_sync(0xffffffffu, done)) break;
-  }
-  // Ritz values: eigenvalues of V^H B V of the last step (FP32)
-  {
-    float2 Hh[R][R];   // Hermitian part of V^H B V (the Jacobi below assumes it)
+    ritz_values<R>(H, lam);
+    float rs = 0.f;
 #pragma unroll
-    for (int m = 0; m < R; ++m)
-#pragma unroll
-      for (int mp = 0; mp < R; ++mp)
-        Hh[m][mp] = make_float2(0.5f * (H[m][mp].x + H[mp][m].x), 0.5f * (H[m][mp].y - H[mp][m].y));
-    if constexpr (R == 1) {
-      lam[0] = Hh[0][0].x;
-    } else if constexpr (R == 2) {
-      // the larger root directly, the smaller as det / larger (no cancellation)
-      const float a = Hh[0][0].x, d = Hh[1][1].x, h = 0.5f * (a - d), m = 0.5f * (a + d);
-      const float r = sqrtf(h * h + cabs2(Hh[0][1]));
-      const float det = a * d - cabs2(Hh[0][1]);
-      lam[0] = m + r;
-      lam[1] = (m + r != 0.f) ? det / (m + r) : m - r;
-    } else if constexpr (R == 3) {
-      // closed form (trigonometric solution of the characteristic cubic of
-      // the shifted, scaled matrix (H - q I) / p, q = tr H / 3): the three
-      // Ritz values are well separated relative to the largest here, so its
-      // single-precision rounding is far inside the tolerance of lambda_B
-      const float a11 = Hh[0][0].x, a22 = Hh[1][1].x, a33 = Hh[2][2].x;
-      const float2 a12 = Hh[0][1], a13 = Hh[0][2], a23 = Hh[1][2];
-      const float q = (a11 + a22 + a33) * (1.f / 3.f);
-      const float b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
-      const float s12 = cabs2(a12), s13 = cabs2(a13), s23 = cabs2(a23);
-      const float p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (s12 + s13 + s23);
-      if (!(p2 > 0.f)) {
-        lam[0] = lam[1] = lam[2] = q;
-      } else {
-        const float p = sqrtf(p2 * (1.f / 6.f));
-        const float2 t = cmul(a12, a23);
-        const float det = b11 * b22 * b33 + 2.f * (t.x * a13.x + t.y * a13.y) - b11 * s23 -
-                          b22 * s13 - b33 * s12;   // det(H - q I)
-        const float r = fminf(1.f, fmaxf(-1.f, det / (2.f * p * p * p)));
-        const float phi = acosf(r) * (1.f / 3.f);
-        const float l1 = q + 2.f * p * cosf(phi);
-        const float l3 = q + 2.f * p * cosf(phi + 2.0943951f);   // + 2 pi / 3
-        lam[0] = l1;
-        lam[1] = 3.f * q - l1 - l3;
-        lam[2] = l3;
-      }
-    } else {
-      float dd[R];
-      float2 UU[R][R];
-      // eigenvalues only; an off-diagonal remainder of 1e-5 |diag| moves them
-      // by ~1e-10 lambda_1^2 / gap
-      jacobi_small<R, false>(Hh, dd, UU, 1e-10f);
-#pragma unroll
-      for (int m = 0; m < R; ++m) lam[m] = dd[m];
-    }
+    for (int m = 0; m < R; ++m) rs += lam[m];
+    const float c = sqrtf(change);
+    const float rho = (lam[R - 1] > 0.f) ? fminf(fmaxf(trB - rs, 0.f) / lam[R - 1], 0.99f)
+                                         : (c > 0.f ? 0.99f : 0.f);
+    converged = converged || c * rho < kSubTol * (1.f - rho);
+    if (__all_sync(0xffffffffu, converged)) break;
   }
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     uh[m] = make_float2(U[m].re.hi, U[m].im.hi);
     ul[m] = make_float2(U[m].re.lo, U[m].im.lo);
   }
+  return converged;
+}
+
+// ------------------------------------------------ ill-gapped B -------------
+// EIG_{r_b} (Sec. 4) of a cell whose eigenvalue lambda_{R+1} lies close to
+// lambda_R, where subspace iteration on R vectors crawls: block subspace
+// iteration with K = min(Q, 8) vectors in float-float (kRrSteps steps; the
+// error of the leading R directions contracts by lambda_{K+1} / lambda_R per
+// step, and for Q <= 8 the block is the whole space), then Rayleigh-Ritz: the
+// K x K matrix V^H B V, diagonalised by a single-precision Jacobi (warm
+// start) and FP64 Jacobi sweeps on the rotated matrix, so that nearly equal
+// Ritz values are separated at double precision.  One warp per cell, lane j
+// < Q = row j.
+constexpr int kRrMaxK = 8;
+constexpr int kRrSteps = 4;
+__host__ __device__ constexpr int rr_k(int q) { return q < kRrMaxK ? q : kRrMaxK; }
+// shared memory of one warp: the bases V and Y = B V [K][Q] float-float
+// complex (16 B), and four K x K matrices (FP64 H and Z1, FP32 H and Z0, 16 B
+// slots)
+__host__ __device__ constexpr int rr_bytes(int q) {
+  return 2 * rr_k(q) * q * 16 + 4 * rr_k(q) * rr_k(q) * 16;
+}
+
+template <typename T>
+struct cpx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ cpx<T> cpx_mul(cpx<T> a, cpx<T> b) {
+  return cpx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cpx_conj(cpx<T> a) { return cpx<T>{a.re, -a.im}; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Cyclic Jacobi on a K x K Hermitian matrix A (shared memory, row-major, full
+// storage) by one warp.  Every lane computes each rotation's parameters from
+// the same 2 x 2 block, so all branches are uniform; lane k < K then rotates
+// entries (k, p), (k, q) and mirrors them, and row k of Z.  On return
+// A = Z^H A_in Z (Z = I at entry if init_z, else Z is right-multiplied).
+// Stops when sum_{i<j} |A_ij|^2 <= tol2 sum_i A_ii^2, or after max_sweeps;
+// an entry |A_pq| <= skip (|A_pp| + |A_qq|) is set to zero, not rotated.
+template <typename T, int K>
+__device__ void jacobi_warp(cpx<T>* A, cpx<T>* Z, int lane, T tol2, T skip, int max_sweeps,
+                            bool init_z) {
+  if (init_z) {
+    for (int e = lane; e < K * K; e += 32) Z[e] = cpx<T>{(e / K == e % K) ? T(1) : T(0), T(0)};
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0), diag = T(0);
+    for (int e = lane; e < K * K; e += 32) {
+      const int r = e / K, c = e % K;
+      if (r == c) diag += A[e].re * A[e].re;
+      if (r < c) off += A[e].re * A[e].re + A[e].im * A[e].im;
+    }
+    off = warp_sum_t(off);
+    diag = warp_sum_t(diag);
+    if (off <= tol2 * diag) break;
+    for (int p = 0; p < K - 1; ++p) {
+      for (int q = p + 1; q < K; ++q) {
+        const cpx<T> b = A[p * K + q];
+        const T app = A[p * K + p].re, aqq = A[q * K + q].re;
+        const T ab = hypot(b.re, b.im);
+        __syncwarp();
+        if (!(ab > skip * (fabs(app) + fabs(aqq)))) {
+          if (lane == 0) A[p * K + q] = A[q * K + p] = cpx<T>{T(0), T(0)};
+          __syncwarp();
+          continue;
+        }
+        const cpx<T> ph = cpx<T>{b.re / ab, b.im / ab};
+        const T tau = (aqq - app) / (T(2) * ab);
+        const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+        const T c = T(1) / sqrt(T(1) + t * t);
+        const T s = t * c;
+        const cpx<T> cph = cpx_conj(ph);
+        if (lane < K) {
+          const int k = lane;
+          if (k != p && k != q) {
+            const cpx<T> akp = A[k * K + p];
+            const cpx<T> x = cpx_mul(cph, A[k * K + q]);
+            const cpx<T> nkp{c * akp.re - s * x.re, c * akp.im - s * x.im};
+            const cpx<T> nkq{s * akp.re + c * x.re, s * akp.im + c * x.im};
+            A[k * K + p] = nkp;
+            A[p * K + k] = cpx_conj(nkp);
+            A[k * K + q] = nkq;
+            A[q * K + k] = cpx_conj(nkq);
+          }
+          const cpx<T> up = Z[k * K + p];
+          const cpx<T> x = cpx_mul(cph, Z[k * K + q]);
+          Z[k * K + p] = cpx<T>{c * up.re - s * x.re, c * up.im - s * x.im};
+          Z[k * K + q] = cpx<T>{s * up.re + c * x.re, s * up.im + c * x.im};
+        }
+        __syncwarp();
+        if (lane == 0) {
+          A[p * K + p] = cpx<T>{app - t * ab, T(0)};
+          A[q * K + q] = cpx<T>{aqq + t * ab, T(0)};
+          A[p * K + q] = A[q * K + p] = cpx<T>{T(0), T(0)};
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ cff cff_warp_sum(cff v) { return cff{ff_warp_sum(v.re), ff_warp_sum(v.im)}; }
+
+// Modified Gram-Schmidt, applied twice, on the K float-float columns of
+// X [K][Q] (shared memory; lane j < Q holds row j, other lanes contribute
+// zeros to the warp sums).
+template <int Q, int K>
+__device__ void mgs2_ff(cff* __restrict__ X, int lane) {
+  const bool row = lane < Q;
+  for (int m = 0; m < K; ++m) {
+    cff x = row ? X[m * Q + lane] : cff_zero();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int mp = 0; mp < m; ++mp) {
+        const cff u = row ? X[mp * Q + lane] : cff_zero();
+        const cff c = cff_warp_sum(cff_cmul(u, x));
+        x = cff_sub(x, cff_mul(u, c));
+      }
+    }
+    const ff n2 = ff_warp_sum(ff_add(ff_mul(x.re, x.re), ff_mul(x.im, x.im)));
+    const ff nrm = ff_sqrt(n2);
+    const ff inv = (nrm.hi > 0.f) ? ff_div(ff{1.f, 0.f}, nrm) : ff{0.f, 0.f};
+    if (row) X[m * Q + lane] = cff_scale(x, inv);
+    __syncwarp();
+  }
+}
+
+// Y[:, m] = B X[:, m] for m < K, float-float (lane j < Q computes row j).
+template <int Q, int K>
+__device__ void b_times_block_ff(const float4* __restrict__ Bc, const cff* __restrict__ X,
+                                 cff* __restrict__ Y, int lane) {
+  if (lane < Q) {
+    for (int m = 0; m < K; ++m) {
+      cff s = cff_zero();
+      for (int l = 0; l < Q; ++l) {
+        const float4 b = b_at<Q>(Bc, lane, l);
+        s = cff_add(s, cff_mul(cff{ff_make(b.x, b.z), ff_make(b.y, b.w)}, X[m * Q + l]));
+      }
+      Y[m * Q + lane] = s;
+    }
+  }
+  __syncwarp();
+}
+
+// Noinline: its registers and spills stay out of the B pass's main path.
+template <int Q, int R>
+__device__ __noinline__ void eig_block_rr(const float4* __restrict__ Bc,
+                                          unsigned char* __restrict__ scr, int lane,
+                                          float2 (&uh)[R], float2 (&ul)[R], float (&lam)[R]) {
+  constexpr int K = rr_k(Q);
+  cff* Vs = reinterpret_cast<cff*>(scr);                                   // [K][Q]
+  cff* Ys = Vs + K * Q;                                                    // [K][Q]
+  cpx<double>* Hd = reinterpret_cast<cpx<double>*>(Ys + K * Q);            // [K][K]
+  cpx<double>* Z1 = Hd + K * K;                                            // [K][K]
+  cpx<float>* Hf = reinterpret_cast<cpx<float>*>(Z1 + K * K);              // [K][K]
+  cpx<float>* Z0 = reinterpret_cast<cpx<float>*>(reinterpret_cast<cpx<double>*>(Hf) + K * K);
+  const bool row = lane < Q;
+  const int j = row ? lane : 0;
+  if constexpr (K == Q) {
+    // the block is the whole space: V = I, V^H B V = B
+    for (int e = lane; e < K * K; e += 32) {
+      const float4 b = b_at<Q>(Bc, e / K, e % K);
+      Hd[e] = cpx<double>{(double)b.x + (double)b.z,
+                          (e / K == e % K) ? 0.0 : (double)b.y + (double)b.w};
+    }
+  } else {
+    // start: K columns of B spread over the window, orthonormalised
+    if (row) {
+      for (int m = 0; m < K; ++m) {
+        const float4 b = b_at<Q>(Bc, j, (m * Q) / K);
+        Vs[m * Q + j] = cff{ff_make(b.x, b.z), ff_make(b.y, b.w)};
+      }
+    }
+    __syncwarp();
+    mgs2_ff<Q, K>(Vs, lane);
+    for (int step = 0; step < kRrSteps; ++step) {
+      b_times_block_ff<Q, K>(Bc, Vs, Ys, lane);
+      mgs2_ff<Q, K>(Ys, lane);
+      cff* t = Vs;
+      Vs = Ys;
+      Ys = t;
+    }
+    b_times_block_ff<Q, K>(Bc, Vs, Ys, lane);   // Y = B V of the final basis
+    // Ritz matrix H = V^H B V (float-float sums, stored as FP64)
+    for (int m = 0; m < K; ++m)
+      for (int n = m; n < K; ++n) {
+        const cff vm = row ? Vs[m * Q + j] : cff_zero();
+        const cff yn = row ? Ys[n * Q + j] : cff_zero();
+        const cff h = cff_warp_sum(cff_cmul(vm, yn));
+        if (lane == 0) {
+          const double hr = (double)h.re.hi + (double)h.re.lo;
+          const double hi = (double)h.im.hi + (double)h.im.lo;
+          Hd[m * K + n] = cpx<double>{hr, m == n ? 0.0 : hi};
+          if (n != m) Hd[n * K + m] = cpx<double>{hr, -hi};
+        }
+      }
+  }
+  __syncwarp();
+  // single-precision warm start, then FP64 sweeps on Z0^H H Z0.  The
+  // single-precision rotations are unitary only to ~1e-7, which would make
+  // Z0^H H Z0 a congruence rather than a similarity (errors ~1e-7 lambda_1
+  // in the Ritz vectors): Z0 is re-orthonormalised in FP64 first (Zd, in
+  // the then dead FP32 H's slots).
+  for (int e = lane; e < K * K; e += 32)
+    Hf[e] = cpx<float>{(float)Hd[e].re, (float)Hd[e].im};
+  __syncwarp();
+  jacobi_warp<float, K>(Hf, Z0, lane, 1e-12f, 1e-9f, 10, true);
+  cpx<double>* Zd = reinterpret_cast<cpx<double>*>(Hf);   // [K][K], FP64 unitary warm start
+  {
+    // lane k < K holds row k; modified Gram-Schmidt twice over the columns
+    const bool zr = lane < K;
+    cpx<double> z[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m)
+      z[m] = zr ? cpx<double>{(double)Z0[lane * K + m].re, (double)Z0[lane * K + m].im}
+                : cpx<double>{0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+        for (int mp = 0; mp < m; ++mp) {
+          // c = z_mp^H z_m
+          const double cr = warp_sum_t(z[mp].re * z[m].re + z[mp].im * z[m].im);
+          const double ci = warp_sum_t(z[mp].re * z[m].im - z[mp].im * z[m].re);
+          z[m].re -= z[mp].re * cr - z[mp].im * ci;
+          z[m].im -= z[mp].re * ci + z[mp].im * cr;
+        }
+      }
+      const double n2 = warp_sum_t(z[m].re * z[m].re + z[m].im * z[m].im);
+      const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+      z[m].re *= inv;
+      z[m].im *= inv;
+    }
+    __syncwarp();
+    if (zr) {
+#pragma unroll
+      for (int m = 0; m < K; ++m) Zd[lane * K + m] = z[m];
+    }
+  }
+  __syncwarp();
+  // Z1 <- H Zd, then Hd <- Zd^H Z1 (FP64)
+  for (int e = lane; e < K * K; e += 32) {
+    const int r = e / K, c = e % K;
+    cpx<double> s{0.0, 0.0};
+    for (int m = 0; m < K; ++m) {
+      const cpx<double> t = cpx_mul(Hd[r * K + m], Zd[m * K + c]);
+      s.re += t.re;
+      s.im += t.im;
+    }
+    Z1[e] = s;
+  }
+  __syncwarp();
+  for (int e = lane; e < K * K; e += 32) {
+    const int r = e / K, c = e % K;
+    cpx<double> s{0.0, 0.0};
+    for (int m = 0; m < K; ++m) {
+      const cpx<double> t = cpx_mul(cpx_conj(Zd[m * K + r]), Z1[m * K + c]);
+      s.re += t.re;
+      s.im += t.im;
+    }
+    s.im = (r == c) ? 0.0 : s.im;
+    Hd[e] = s;   // no lane reads Hd in this loop
+  }
+  __syncwarp();
+  // Hermitise (the two triangles of Z0^H H Z0 differ by rounding)
+  for (int e = lane; e < K * K; e += 32) {
+    const int r = e / K, c = e % K;
+    if (r < c) {
+      const cpx<double> a = Hd[r * K + c], b = Hd[c * K + r];
+      const cpx<double> h{0.5 * (a.re + b.re), 0.5 * (a.im - b.im)};
+      Hd[r * K + c] = h;
+      Hd[c * K + r] = cpx_conj(h);
+    }
+  }
+  __syncwarp();
+  jacobi_warp<double, K>(Hd, Z1, lane, 1e-30, 1e-20, 6, true);
+  // leading R Ritz values (every lane ranks the same diagonal)
+  int sel[R];
+  {
+    double d[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) d[m] = Hd[m * K + m].re;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int best = 0;
+      double bv = -1e300;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        bool taken = false;
+#pragma unroll
+        for (int rr = 0; rr < r; ++rr) taken |= (sel[rr] == m);
+        if (!taken && d[m] > bv) {
+          bv = d[m];
+          best = m;
+        }
+      }
+      sel[r] = best;
+      lam[r] = (float)bv;
+    }
+  }
+  // U[:, r] = V Zd Z1[:, sel[r]]: w = Zd Z1[:, sel r] (K, FP64), then row j of V w
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double ur = 0.0, ui = 0.0;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      cpx<double> w{0.0, 0.0};
+      for (int n = 0; n < K; ++n) {
+        const cpx<double> t = cpx_mul(Zd[m * K + n], Z1[n * K + sel[r]]);
+        w.re += t.re;
+        w.im += t.im;
+      }
+      double vr, vi;
+      if constexpr (K == Q) {
+        vr = (m == j) ? 1.0 : 0.0;
+        vi = 0.0;
+      } else {
+        const cff v = Vs[m * Q + j];
+        vr = (double)v.re.hi + (double)v.re.lo;
+        vi = (double)v.im.hi + (double)v.im.lo;
+      }
+      ur += vr * w.re - vi * w.im;
+      ui += vr * w.im + vi * w.re;
+    }
+    const float hr = (float)ur, hi = (float)ui;
+    uh[r] = make_float2(hr, hi);
+    ul[r] = make_float2((float)(ur - (double)hr), (float)(ui - (double)hi));
+  }
 }
 
 // Threads of a B-pass CTA: 512 at q = 32, where the tile's B matrices fill
 // most of shared memory and one CTA per SM must bring its own 16 warps.
 __host__ __device__ constexpr int bfit_threads(int q) { return q >= 32 ? 512 : kThreads; }
+
+constexpr int kLagStages = 4;   // lag-store prefetch depth of the B pass
+
+
+
+// Shared memory of the B pass after the tile's B and a: the lag buffers
+// (and, when the lags are recomputed, the box-sum buffers and the
+// fixed-point tile), reused by the eigen phase's bases and then by the block
+// Rayleigh-Ritz scratch of ill-gapped cells (at least one warp's worth).
+// Host and device size it with the same functions.
+__host__ __device__ constexpr int bfit_lag_bytes(int P, int Q, int TC, int Ra, bool from_store) {
+  return (from_store ? kLagStages : 1) * P * P * (TC + Q - 1) * 16 +
+         (from_store ? 0 : 2 * P * P * (TC + 2 * Ra + Q - 1) * 16);
+}
+__host__ __device__ constexpr int bfit_basis_bytes(int Q, int R) {
+  return (bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;
+}
+__host__ __device__ constexpr int imax3(int a, int b, int c) {
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+// The region from the lag buffers' start: lags or bases or fallback scratch,
+// then (recompute variant only) the fixed-point tile, which is dead by the
+// eigen phase and counts toward the fallback scratch.
+__host__ __device__ constexpr int bfit_region_bytes(int P, int Q, int R, int TC, int Ra, int Rr,
+                                                     bool from_store) {
+  return imax3(bfit_lag_bytes(P, Q, TC, Ra, from_store), bfit_basis_bytes(Q, R), rr_bytes(Q)) +
+         (from_store ? 0 : P * (2 * Rr + 1) * (TC + 2 * Ra + Q - 1) * 8);
+}
 
 // 16-byte asynchronous global -> shared copy; valid == false zero-fills the
 // destination (src is then not read but must still be a mapped address).
@@ -1122,15 +1525,13 @@ struct BAcc {
   }
 };
 
-constexpr int kLagStages = 4;   // lag-store prefetch depth of the B pass
-
 // CTA = one row of tc cells.  B phase: for each lag, the tile's lag sums
 // (read from the lag store with a double-buffered cp.async prefetch of the
 // next lag, or recomputed from Y) are contracted with each cell's a into the
 // diagonal of B, two entries per thread at a time (independent float-float
 // chains).  Eigen phase: one group of Q lanes per cell.
 template <int P, int Q, int R, bool FROM_STORE>
-__global__ void __launch_bounds__(bfit_threads(Q))
+__global__ void __launch_bounds__(bfit_threads(Q), 65536 / 128 / bfit_threads(Q))
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
@@ -1259,36 +1660,65 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
     }
   }
 
-  // eigen phase: a group of Q lanes per cell
+  // eigen phase: a group of Q lanes per cell; cells whose subspace iteration
+  // does not converge (ill-gapped B) are queued for the block Rayleigh-Ritz
+  // phase below
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / Q, j = lane % Q;
   const int slot = warp * CPW + sub;
   const int per_pass = (NT / 32) * CPW;
+  // writes U_B (row j of cell cl) and, from lane j == 0, lambda_B
+  auto store = [&](int cl, int jj, const float2 (&uh)[R], const float2 (&ul)[R],
+                   const float (&lam)[R]) {
+    const size_t cell = (size_t)r * g.W + (c0 + cl);   // this job's cell index
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      UBh[(cell * Q + jj) * R + m] = uh[m];
+      UBl[(cell * Q + jj) * R + m] = ul[m];
+    }
+    if (jj == 0 && lamB) {
+      // B^ = b / |a|^2 in S units, then tr A^ = p normalisation
+      float an = 0.f, tr = 0.f;
+      for (int J = 0; J < PP; ++J) an += cabs2(make_float2(as[cl * PP + J].x, as[cl * PP + J].w));
+      for (int i = 0; i < P; ++i) tr += as[cl * PP + i * (P + 1)].x;
+      const float unit = ldexpf(1.f, 60 - 2 * sh) / (float)g.n;
+      const float f = (an > 0.f) ? unit / an * tr / (float)P : 0.f;
+#pragma unroll
+      for (int m = 0; m < R; ++m) lamB[cell * R + m] = lam[m] * f;
+    }
+  };
+  __shared__ int fb_n;
+  __shared__ int fb_cell[kTileCells];
+  if (threadIdx.x == 0) fb_n = 0;
+  __syncthreads();
   for (int base = 0; base < TC; base += per_pass) {
     const int cl = base + slot;
     const bool live = cl < TC && (c0 + cl) < g.W;
     const int clc = live ? cl : 0;
     float2 uh[R], ul[R];
     float lam[R];
-    eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
-    if (live) {
-      const size_t cell = (size_t)r * g.W + (c0 + cl);   // this job's cell index
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        UBh[(cell * Q + j) * R + m] = uh[m];
-        UBl[(cell * Q + j) * R + m] = ul[m];
-      }
-      if (j == 0 && lamB) {
-        // B^ = b / |a|^2 in S units, then tr A^ = p normalisation
-        float an = 0.f, tr = 0.f;
-        for (int J = 0; J < PP; ++J) an += cabs2(make_float2(as[cl * PP + J].x, as[cl * PP + J].w));
-        for (int i = 0; i < P; ++i) tr += as[cl * PP + i * (P + 1)].x;
-        const float unit = ldexpf(1.f, 60 - 2 * sh) / (float)g.n;
-        const float f = (an > 0.f) ? unit / an * tr / (float)P : 0.f;
-#pragma unroll
-        for (int m = 0; m < R; ++m) lamB[cell * R + m] = lam[m] * f;
+    const bool conv = eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
+    if (live && conv) store(cl, j, uh, ul, lam);
+    if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
+  }
+  __syncthreads();
+  const int nfb = fb_n;
+  if (nfb > 0) {
+    // one warp per queued cell, each with rr_bytes(Q) of the (now dead) lag
+    // and basis scratch
+    const int slots = min(NT / 32, bfit_region_bytes(P, Q, R, TC, g.Ra, g.Rr, FROM_STORE) / rr_bytes(Q));
+    if (warp < slots) {
+      for (int e = warp; e < nfb; e += slots) {
+        const int cl = fb_cell[e];
+        float2 uh[R], ul[R];
+        float lam[R];
+        eig_block_rr<Q, R>(Bs + cl * NB, reinterpret_cast<unsigned char*>(lag) + warp * rr_bytes(Q),
+                           lane, uh, ul, lam);
+        if (lane < Q) store(cl, lane, uh, ul, lam);
+        __syncwarp();
       }
     }
+    if (threadIdx.x == 0 && JL.report) atomicAdd(JL.report + 2, (unsigned long long)nfb);
   }
   __syncthreads();
   }  // tile loop

@@ -331,6 +331,12 @@ k_flipflop_t(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* _
         if (m < ra)
           s = cadd(s, cscale(cmul(Ut[(i * RA + m) * nt + tid], cconj(Ut[(k * RA + m) * nt + tid])),
                              dt[m]));
+      // exactly Hermitian (the B pass mirrors the upper triangle of B, which
+      // is the Hermitian part of b only for a Hermitian a): entry (i, k) with
+      // i < k is the conjugate of its mirror (k, i), already updated in this
+      // loop (k + P i < i + P k), and the diagonal is real
+      if (i < k) s = cconj(a_[(k + P * i) * nt]);
+      if (i == k) s.y = 0.f;
       dn += cabs2(csub(s, a_[J * nt]));
       nn += cabs2(s);
       a_[J * nt] = s;

@@ -50,7 +50,7 @@ def test_nonfinite_samples_flag_their_cells_only():
     Y[0, 5, 70] = complex(1.0, np.inf)
     Y[2, 45, 10] = complex(-np.inf, 0.0)
     f = dataclasses.replace(f, Y=Y)
-    gpu, (nonconv, nonfinite) = _run(f)
+    gpu, (nonconv, nonfinite, _) = _run(f)
     flag = _box_flags(wl, bad)
     assert 0 < flag.sum() < flag.size
     assert nonfinite == int(flag.sum())
@@ -75,7 +75,7 @@ def test_all_zero_frame():
     wl = gen.WORKLOADS["frame1024"].with_size(9, 40)
     f = gen.make_frame(wl)
     f = dataclasses.replace(f, Y=np.zeros_like(f.Y))
-    gpu, (nonconv, nonfinite) = _run(f)
+    gpu, (nonconv, nonfinite, _) = _run(f)
     assert nonfinite == 0
     assert (gpu["Tmax"] == 0).all() and (gpu["T_all"] == 0).all()
     assert (gpu["vidx"] == 0).all() and (gpu["map"] == 0).all()
@@ -87,12 +87,12 @@ def test_iteration_cap_reported():
     that had not met eps, and iters never exceeds the cap."""
     wl = gen.WORKLOADS["small64"].with_size(16, 24)
     f = gen.make_frame(wl)
-    gpu, (nonconv, nonfinite) = _run(f, max_iter=1)
+    gpu, (nonconv, nonfinite, _) = _run(f, max_iter=1)
     assert gpu["iters"].max() == 1
     assert 0 < nonconv <= wl.H * wl.W
     assert nonfinite == 0
     # with the default cap every cell converges and the report is clean
-    gpu, (nonconv, _) = _run(f, T_all=False)
+    gpu, (nonconv, _, _) = _run(f, T_all=False)
     assert nonconv == 0 and gpu["iters"].max() < 64
 
 
@@ -104,6 +104,6 @@ def test_largest_training_box_q32():
                              ring_a=19, guard_r=1, guard_a=2, n_targets=2)
     f = gen.make_frame(wl)
     ref = oracle.run_workload(f)
-    gpu, (nonconv, nonfinite) = _run(f)
+    gpu, (nonconv, nonfinite, _) = _run(f)
     assert nonconv == 0 and nonfinite == 0
     compare(gpu, ref, np.arange(wl.H * wl.W), wl.tau)
