@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kstap", choices=["kstap", "reference"])
+    ap.add_argument("--peaks", metavar="PATH",
+                    help="measure the arithmetic pipes (FP32 and packed f32x2 FMA, 64-bit "
+                         "integer multiply-add, FP64 FMA) with kstap_alu_probe, write their "
+                         "peaks to PATH (JSON) and exit")
     ap.add_argument("--workload", default="frame1024")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "bf16x3"],
                     help="arithmetic of the velocity-bank contraction (fp32: CUDA cores; "
@@ -182,6 +186,57 @@ class ClockSampler:
                           if r[5 + i].lower().startswith("active")})
         return dict(sm_mhz=statistics.median(sm) if sm else None,
                     sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+
+
+# ------------------------------------------------------------- ALU peaks ---
+PEAKS_FILE = os.path.join(ROOT, "peaks.json")
+
+
+def measure_peaks(path: str, seconds: float = 3.0):
+    """Throughput of each arithmetic pipe on cuda:0 (kstap_alu_probe), about
+    `seconds` of launches per pipe with the SM clock sampled meanwhile; the
+    result (ops/s, flop rates, median MHz) is written to `path`."""
+    import torch
+    import paper_1604_03622_b300 as K
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = dict(device=torch.cuda.get_device_name(0), sms=torch.cuda.get_device_properties(0)
+               .multi_processor_count, when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+               how="kstap_alu_probe: SMs x 8 CTAs x 256 threads, 8 independent chains per "
+                   "thread, CUDA events over ~%.0f s of launches per pipe" % seconds)
+    for op, iters in (("ffma", 1 << 16), ("ffma2", 1 << 16), ("imad64", 1 << 13),
+                      ("dfma", 1 << 10)):
+        rate = K.kstap_alu_probe(op, iters, 4, stream)          # warm-up and calibration
+        per_launch = (out["sms"] * 8 * 256 * iters * 8 * (2 if op == "ffma2" else 1)) / rate
+        reps = max(4, int(seconds / per_launch))
+        clk = ClockSampler(0, True)
+        rate = K.kstap_alu_probe(op, iters, reps, stream)
+        c = clk.stop() or {}
+        out[op] = dict(ops_per_s=rate, iters=iters, reps=reps, sm_mhz=c.get("sm_mhz"),
+                       sm_max_mhz=c.get("sm_max_mhz"), reasons=c.get("reasons"))
+    out["fp32_fma_tflops"] = 2 * max(out["ffma"]["ops_per_s"], out["ffma2"]["ops_per_s"]) / 1e12
+    out["fp32_fma_mhz"] = (out["ffma2"] if out["ffma2"]["ops_per_s"] >= out["ffma"]["ops_per_s"]
+                           else out["ffma"])["sm_mhz"]
+    out["imad64_tops"] = out["imad64"]["ops_per_s"] / 1e12
+    out["fp64_fma_tflops"] = 2 * out["dfma"]["ops_per_s"] / 1e12
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out), flush=True)
+
+
+def alu_peak():
+    """(FP32 FMA peak TFLOP/s, the median SM MHz it was measured at, note) from
+    peaks.json, else the unit-count figure at the maximum clock."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            pk = json.load(fh)
+        mhz = pk.get("fp32_fma_mhz") or 2032.0
+        return (float(pk["fp32_fma_tflops"]), float(mhz),
+                "measured: FP32 FMA peak of kstap_alu_probe (bench.py --peaks, peaks.json) at "
+                "%.0f MHz median SM clock (%s)" % (mhz, pk.get("when", "")))
+    except (OSError, KeyError, ValueError):
+        return (148 * 128 * 2 * 2032e6 / 1e12, 2032.0,
+                "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz (no peaks.json)")
 
 
 # ------------------------------------------------------------ work model ---
@@ -648,6 +703,9 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
 # ------------------------------------------------------------------ main ----
 def main():
     args = parse()
+    if args.peaks:
+        measure_peaks(args.peaks)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -767,16 +825,15 @@ def main():
     achieved = work[dom] * ncell / (per_launch_ms / 1e3) / 1e12
     traffic_bytes, traffic_src = measured_traffic(wl.name, args.precision, dom)
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
-    peak_clock = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FP32 FMA: 128 lanes/SM
-    peak_max = 148 * 128 * 2 * 2032e6 / 1e12
-    roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak_max, unit="TFLOP/s",
-                frac=achieved / peak_max, frac_at_measured_clock=achieved / peak_clock,
+    peak, peak_mhz, peak_note = alu_peak()
+    peak_clock = peak * sm_mhz / peak_mhz                  # the same pipe at this run's clock
+    roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=achieved / peak, frac_at_measured_clock=achieved / peak_clock,
                 traffic=traffic_bytes, traffic_source=traffic_src,
                 issue_active_ncu=measured_traffic(wl.name, args.precision, dom, "issue_active")[0],
                 fma_pipe_active_ncu=measured_traffic(wl.name, args.precision, dom,
                                                      "fma_pipe_active")[0],
-                peak_note="148 SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock); "
-                          "no measured FP32 peak in MEASURED_PEAKS.json",
+                peak_note=peak_note,
                 kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()},
                 kernel_share={k: v[0] / max(sum(x[0] for x in kt.values()), 1e-9)
                               for k, v in kt.items()})

@@ -203,6 +203,21 @@ enum {
 kstap_status kstap_set_profiling(kstap_ctx* ctx, int enable);
 kstap_status kstap_kernel_times(kstap_ctx* ctx, float* total_ms, int32_t* launches, int n);
 
+/* Throughput probe of one arithmetic pipe, the measured denominator of the
+ * kernels' roofline fractions (the paper has no counterpart): op
+ * KSTAP_PROBE_FFMA (FP32 fused multiply-add), KSTAP_PROBE_FFMA2 (packed
+ * f32x2 FMA, both lanes counted), KSTAP_PROBE_IMAD64 (64-bit integer
+ * multiply-add, the arithmetic of the exact lag sums) or KSTAP_PROBE_DFMA
+ * (FP64 FMA).  Every thread of SMs x 8 CTAs x 256 threads runs 8 independent
+ * chains of `iters` operations (rounded down to a multiple of 4); one warm-up
+ * launch, then `reps` launches timed with CUDA events on cuda_stream.
+ * *ops_per_s = operations per second (one FMA or multiply-add per lane = one
+ * operation; a flop rate is twice that).  Allocates an 8-byte counter
+ * stream-ordered; synchronises the stream.  iters < 4, reps < 1, an unknown
+ * op or a NULL ops_per_s give KSTAP_EINVAL. */
+enum { KSTAP_PROBE_FFMA = 0, KSTAP_PROBE_FFMA2 = 1, KSTAP_PROBE_IMAD64 = 2, KSTAP_PROBE_DFMA = 3 };
+kstap_status kstap_alu_probe(int op, int iters, int reps, void* cuda_stream, double* ops_per_s);
+
 /* ------------------------------------------------------------ batches ----
  * One frame of a batch: the frame Y (device, p x H_in x W_in complex64), its
  * caller-owned factor arrays and outputs (device, H * W cells; layouts as in

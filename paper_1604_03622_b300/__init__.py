@@ -25,7 +25,7 @@ EXPORTED = ["kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy"
             "kstap_graph_create", "kstap_graph_launch", "kstap_graph_destroy", "kstap_autotune",
             "kstap_set_tuning", "kstap_serve_config", "kstap_submit", "kstap_poll",
             "kstap_release", "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
-            "kstap_change_map", "kstap_serve_batch_cells"]
+            "kstap_change_map", "kstap_serve_batch_cells", "kstap_alu_probe"]
 KERNELS = ["frame_scale", "moments", "flipflop", "bfit", "detect", "mgram"]
 
 
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
         L.kstap_fit_report.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]
+        L.kstap_alu_probe.argtypes = [I, I, I, P, ctypes.POINTER(ctypes.c_double)]
         L.kstap_set_profiling.argtypes = [P, I]
         L.kstap_kernel_times.argtypes = [P, P, P, I]
         for name in ("kstap_create", "kstap_fit_project", "kstap_detect", "kstap_destroy",
@@ -121,7 +122,7 @@ def lib() -> ctypes.CDLL:
                      "kstap_graph_destroy", "kstap_autotune", "kstap_set_tuning",
                      "kstap_serve_config", "kstap_submit", "kstap_poll", "kstap_release",
                      "kstap_fit_report", "kstap_device_status", "kstap_lrkron_fit",
-                     "kstap_change_map", "kstap_serve_batch_cells"):
+                     "kstap_change_map", "kstap_serve_batch_cells", "kstap_alu_probe"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -191,6 +192,17 @@ def kstap_lrkron_fit(X, r_a: int = 1, eps: float = 1e-6, max_iter: int = 100, A_
     _check(lib().kstap_lrkron_fit(_ptr(X), n, p, q, r_a, float(eps), int(max_iter), _ptr(A_out),
                                   _ptr(B_out), ctypes.byref(it), ctypes.byref(et), stream or None))
     return A_out, B_out, int(it.value), float(et.value)
+
+
+PROBES = {"ffma": 0, "ffma2": 1, "imad64": 2, "dfma": 3}
+
+
+def kstap_alu_probe(op: str, iters: int, reps: int, stream: int = 0) -> float:
+    """Operations per second of one arithmetic pipe (op in PROBES; one FMA or
+    multiply-add per lane = one operation); synchronises the stream."""
+    out = ctypes.c_double()
+    _check(lib().kstap_alu_probe(PROBES[op], int(iters), int(reps), stream, ctypes.byref(out)))
+    return float(out.value)
 
 
 def kstap_change_map(T_all, V: int, K: int, Tmax_k=None, change=None, stream: int = 0):

@@ -33,7 +33,8 @@ def nvcc() -> str:
 
 def units():
     """(object name, source, extra defines) of every translation unit."""
-    out = [("kstap_api.o", os.path.join(CSRC, "kstap_api.cu"), [])]
+    out = [("kstap_api.o", os.path.join(CSRC, "kstap_api.cu"), []),
+           ("kstap_peaks.o", os.path.join(CSRC, "kstap_peaks.cu"), [])]
     for p, q in CLASSES:
         for part, name in ((0, "fit"), (1, "detect")):
             out.append((f"kstap_{name}_p{p}_q{q}.o", os.path.join(CSRC, "kstap_inst.cu"),

@@ -39,26 +39,6 @@ def test_tc_parity(precision, name, H, W, r_b):
     print(precision, name, H, W, r_b, rep)
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
-def test_tc_parity_full_size_q32_frame_sampled(precision):
-    """The 2048 x 2048 q = 32 frame with the tensor-core bank, run whole;
-    all velocities on every target cell and 512 random cells, at the route's
-    stated bound."""
-    import torch
-    from gpu_common import run_sampled
-    from paper_1604_03622_b300.runner import KStap
-    wl = gen.WORKLOADS["precision2048"]
-    f = gen.make_frame(wl)
-    tcells = [r * wl.W + c for r, c, _, _ in f.targets]
-    cells = np.unique(np.concatenate([tcells, gen.random_cells(wl, 512, seed=9)]).astype(np.int64))
-    ks = KStap.from_workload(wl, f.bank_a, f.bank_b, precision=precision)
-    gpu = run_sampled(ks, torch.from_numpy(f.Y).cuda(), cells)
-    ks.close()
-    ref = oracle.run_workload(f, cells=cells, want_proj=False)
-    rep = compare(gpu, ref, np.arange(len(cells)), wl.tau, tol=TOL[precision])
-    print(precision, rep)
-
-
 def test_tc_factors_equal_fp32_route():
     """The precision switch changes only the statistic: the fitted factors are
     bit-identical, and T agrees with the FP32 route to the 16-bit bar."""
