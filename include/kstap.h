@@ -168,8 +168,9 @@ kstap_status kstap_detect(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
                           const kstap_factors* factors, float* Tmax, int32_t* vidx, uint8_t* map,
                           float* T_all);
 
-/* Waits for the context stream, then reports whether a tensor-core kernel of
- * this context gave up a bounded wait for its MMAs (KSTAP_ECUDA, with the
+/* Waits for the context stream, then reports whether a kernel of this
+ * context gave up a bounded wait -- a tensor-core kernel waiting for its MMAs,
+ * or the moments pass waiting for a TMA tile load -- (KSTAP_ECUDA, with the
  * reason in kstap_last_error; the word is cleared) or not (KSTAP_OK).
  * Results of a launch that gave up are not valid; if the message says the
  * device state is unknown, the MMAs had not completed when the kernel freed

@@ -17,6 +17,8 @@
 #include <thread>
 #include <unordered_map>
 
+#include <cudaTypedefs.h>
+
 #include "kstap_host.cuh"
 #include "kstap_lrk.cuh"
 #include "kstap_misc.cuh"
@@ -264,6 +266,44 @@ std::vector<Frame> split_rows(const kstap_params& p, int V, const Frame& f, int 
   return out;
 }
 
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+// (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  });
+  return fn;
+}
+
+// The job's 1-D tensor map over its frame as float pairs, from Y to the end
+// of the last channel's last row, with the moments pass's box (one tile row
+// segment).  Left unset (ymap_ok = 0, plain loads) when Y is not 16-byte
+// aligned or the extent does not fit the map's 32-bit signed coordinates.
+void encode_ymap(Job& j, int P, int WT) {
+  j.ymap_ok = 0;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)j.Y & 15)) return;
+  const unsigned long long nf =
+      2ull * ((unsigned long long)(P - 1) * (unsigned long long)j.ch_stride +
+              (unsigned long long)j.H_in * (unsigned long long)j.W_in);
+  if (nf >= (1ull << 31)) return;
+  cuuint64_t dim[1] = {nf};
+  cuuint64_t stride[1] = {0};   // rank 1: no strides
+  cuuint32_t box[1] = {(cuuint32_t)kstap::moments_box_floats(WT)};
+  cuuint32_t es[1] = {1};
+  if (enc(&j.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, (void*)j.Y, dim, stride, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+    j.ymap_ok = 1;
+}
+
 // Fills the jobs of one launch; scratch and L may be null (detect-only).
 void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& fr, char* scratch,
                const Layout* L, std::vector<Job>& jobs, JobList& JL) {
@@ -292,6 +332,7 @@ void fill_jobs(const kstap_params& p, const Geom& g, const std::vector<Frame>& f
     j.vidx = fr[k].vidx;
     j.map = fr[k].map;
     j.T_all = fr[k].T_all;
+    if (scratch) encode_ymap(j, p.p, kstap::kTileCells + 2 * p.ring_a + p.q - 1);
     j.tile0[kstap::kKindMoments] = t[0];
     j.tile0[kstap::kKindFlip] = t[1];
     j.tile0[kstap::kKindBfit] = t[2];
@@ -423,6 +464,7 @@ kstap_status enqueue_batch(kstap_ctx* ctx, kstap_ctx* prof, const std::vector<Fr
   fill_jobs(ctx->prm, g, fr, scratch, &L, host, JL);
   if (fr.size() > 1) JL.table = jobs_dev;
   JL.report = report;
+  JL.fault = ctx->fault;
   kstap_status st = dispatch_fit(ctx, prof, g, JL, scratch, L, true, ctx->sm_count,
                                  ctx->tune.waves, s);
   if (st != KSTAP_OK) return st;
@@ -587,6 +629,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
     JobList JL;
     fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
     JL.report = ctx->report;
+    JL.fault = ctx->fault;
     st = dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
                       ctx->stream);
     if (st != KSTAP_OK) return st;
@@ -887,6 +930,9 @@ kstap_status kstap_device_status(kstap_ctx* ctx) {
     if (f & 2u)
       return fail(ctx, KSTAP_ECUDA, "a tensor-core completion never arrived and the tile's tensor "
                   "memory was freed (fault word 0x%x): the device state is unknown", f);
+    if (f & 4u)
+      return fail(ctx, KSTAP_ECUDA, "a TMA tile load of the moments pass did not complete within "
+                  "its bounded wait (fault word 0x%x)", f);
     return fail(ctx, KSTAP_ECUDA, "a tensor-core completion wait gave up (fault word 0x%x)", f);
   }
   return KSTAP_OK;

@@ -133,9 +133,11 @@ inline size_t smem_moments(const Geom& g) {
   const int NRT = 2 * g.Rr + TR, WT = TC + 2 * g.Ra + g.q - 1, NUmax = TC + g.q - 1;
   size_t b = (size_t)P * NRT * WT * 8;
   b += (b & 15);
-  b += 2 * (size_t)PP * WT * 16;
-  if (P <= 3) b += (size_t)TR * PP * NUmax * 8;   // row lags for the per-thread M
-  return b;
+  // box sums, then the row lags of the per-thread M; the TMA staging of the
+  // frame tile reuses that region, which is grown if the tile is larger
+  size_t region = 2 * (size_t)PP * WT * 16;
+  if (P <= 3) region += (size_t)TR * PP * NUmax * 8;
+  return b + std::max(region, (size_t)kstap::moments_stage_bytes(P, NRT, WT));
 }
 
 inline size_t smem_mgram(const Geom& g) {

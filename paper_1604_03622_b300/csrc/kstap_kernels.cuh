@@ -28,6 +28,7 @@
 //    vectors that keep < 1e-2 of their energy after projection are
 //    re-projected with the float-float U_B.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,6 +64,12 @@ struct Geom {
 enum { kKindMoments = 0, kKindFlip = 1, kKindBfit = 2, kKindDetect = 3, kKindMgram = 4,
        kKinds = 5 };
 struct Job {
+  // 1-D tiled tensor map over this job's frame, as float pairs from Y to the
+  // end of the last channel's last row (TMA tile loads of the moments pass);
+  // ymap_ok = 0 when Y is not 16-byte aligned or the frame exceeds the map's
+  // extent, and that pass then loads its tiles with plain loads
+  CUtensorMap ymap;
+  int ymap_ok;
   const float2* Y;              // first row of this job's rows, channel 0
   int H_in, W_in, H, W;         // rows / columns of this job (a frame or a row strip of one)
   long long ch_stride;          // elements between channel planes
@@ -92,6 +99,7 @@ struct JobList {
   long long NC;                 // total cells (stride of the per-cell workspace arrays)
   unsigned long long* report;   // optional counters: [0] cells at max_iter, [1] cells flagged
                                 // non-finite, [2] cells of the ill-gapped EIG_{r_b} path
+  unsigned* fault;              // optional device word: bit 2 = a TMA tile wait gave up
 };
 
 __device__ __forceinline__ const Job& job_of(const JobList& L, int kind, int tile, int& local) {
@@ -293,6 +301,54 @@ constexpr int kMomRows = 4;                         // cell rows per CTA in the 
 constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
 constexpr int kHChunk = 3;                          // positions per item in the running ring sums
 
+// TMA staging of the moments pass's frame tile.  Each (channel, row) segment
+// of WT complex samples is one load of the job's 1-D tensor map (float
+// elements); a TMA start coordinate must be 16-byte aligned, so a load starts
+// at the even sample at or before the segment and covers WT + 1 samples,
+// rounded up to whole 16-byte units.  A tensor copy's shared-memory
+// destination must be 128-byte aligned: the staging area starts at the first
+// 128-byte boundary of its region and its rows are 128-byte multiples apart.
+// Host and device size the box and the staging area with these functions.
+__host__ __device__ constexpr int moments_box_floats(int WT) { return ((2 * (WT + 1) + 3) / 4) * 4; }
+__host__ __device__ constexpr int moments_stage_row_floats(int WT) {
+  return ((moments_box_floats(WT) + 31) / 32) * 32;
+}
+__host__ __device__ constexpr int moments_stage_bytes(int P, int NRT, int WT) {
+  return P * NRT * moments_stage_row_floats(WT) * 4 + 128;
+}
+constexpr long long kTmaWaitCycles = 1ll << 30;   // ~0.5 s at 2 GHz: bound of one tile wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One 1-D tiled TMA load of the map's box at element x into shared memory,
+// completing on the mbarrier's transaction count.
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, int x,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2}], [%3];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Polls the mbarrier for phase `parity` for at most `cycles` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity,
+                                                  long long cycles) {
+  uint32_t done = 0;
+  const long long t0 = clock64();
+  while (!done && clock64() - t0 < cycles) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
 // ------------------------------------------------ K1a: lag moments ---------
 // CTA = kMomRows cell rows x kTileCells cells, one thread per cell.  The
 // vertical box sums run down the kMomRows rows as exact int64 running sums.
@@ -309,8 +365,8 @@ constexpr int kHChunk = 3;                          // positions per item in the
 // u in [c0, c0 + TC) (the last tile also its halo).
 template <int P, int Q>
 __global__ void __launch_bounds__(kMomThreads)
-k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
-          float4* __restrict__ Lw0) {
+k_moments(const __grid_constant__ Geom g0, const __grid_constant__ JobList JL,
+          float2* __restrict__ Mw, float2* __restrict__ Sw, float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   // the per-thread Gram M (and the block sums) only for P <= 3; for more
   // channels (stacked passes) this pass writes the lag store and k_mgram forms
@@ -320,7 +376,14 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
   constexpr int NS = kThreadM ? PP : 1;
   constexpr int TC = kTileCells;
   constexpr int TR = kMomRows;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t ymbar;   // completion of a tile's TMA loads
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(&ymbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t yphase = 0;
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindMoments]; tile += gridDim.x) {
   int lt;
   const Job& JB = job_of(JL, kKindMoments, tile, lt);
@@ -342,7 +405,54 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
 
   const int sh = frame_shift(*maxbits, g.B);
   const float scale = ldexpf(1.f, sh);
-  {
+  // a tensor map must sit on a 64-byte boundary (it does in the kernel
+  // parameters and in the device job table; plain loads otherwise)
+  if (JB.ymap_ok && (reinterpret_cast<uintptr_t>(&JB.ymap) & 63) == 0) {
+    // TMA: warp 0 arms the mbarrier with the tile's bytes and issues one load
+    // per (channel, row) segment inside the frame into the staging area (the
+    // box-sum buffers, dead until the lag loop); every thread then waits and
+    // converts its samples from the staging rows (offset by the odd start)
+    float* stg = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(Vo) +
+                                          ((128u - (smem_addr(Vo) & 127u)) & 127u));
+    const int BF = moments_stage_row_floats(WT);   // row stride; the box is moments_box_floats
+    const int nin = min(NRT, g.H_in - r0);   // rows inside the frame
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                         smem_addr(&ymbar)),
+                     "r"((unsigned)(P * nin * moments_box_floats(WT) * 4))
+                     : "memory");
+      }
+      __syncwarp();
+      for (int s = threadIdx.x; s < P * nin; s += 32) {
+        const int i = s / nin, rho = s - i * nin;
+        const long long e = (long long)i * g.ch_stride + (long long)(r0 + rho) * g.W_in + c0;
+        tma_load_1d(stg + (i * NRT + rho) * BF, &JB.ymap, (int)((e & ~1ll) * 2), &ymbar);
+      }
+    }
+    if (!mbar_wait_bounded(&ymbar, yphase, kTmaWaitCycles)) {
+      if (JL.fault) atomicOr(JL.fault, 4u);
+      mbar_wait_bounded(&ymbar, yphase, kTmaWaitCycles);
+    }
+    yphase ^= 1u;
+    const int total = P * NRT * WT;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int col = idx % WT;
+      const int rho = (idx / WT) % NRT;
+      const int i = idx / (WT * NRT);
+      const int gr = r0 + rho, gc = c0 + col;
+      int2 v = make_int2(0, 0);
+      if (gc < g.W_in && gr < g.H_in) {
+        const long long e = (long long)i * g.ch_stride + (long long)gr * g.W_in + c0;
+        const float2 y = *reinterpret_cast<const float2*>(
+            stg + (i * NRT + rho) * BF + 2 * (col + (int)(e & 1)));
+        v.x = quantise(y.x, scale);
+        v.y = quantise(y.y, scale);
+      }
+      Yq[idx] = v;
+    }
+  } else {
     const int total = P * NRT * WT;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int col = idx % WT;
@@ -549,6 +659,9 @@ k_moments(Geom g0, JobList JL, float2* __restrict__ Mw, float2* __restrict__ Sw,
     for (int J = 0; J < PP; ++J) Sw[J * ncell + cell] = make_float2(sr[J], si[J]);
   }
   }
+  // this tile's generic-proxy writes to the staging area (box sums, row
+  // lags) are ordered before the next tile's TMA writes into it
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   __syncthreads();
   }  // tile loop
 }
