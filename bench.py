@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg on the 256-tile workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-requests", type=int, default=60,
+    ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests in the Poisson serving stream")
     ap.add_argument("--cells", type=int, nargs=2, metavar=("H", "W"),
                     help="run the workload's model on an H x W cell grid (profiling cases)")
@@ -328,9 +328,9 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
     """256 uneven tiles (q in {8,16,32}, r_b in {2,3,4}): plain = one tile at a
     time through kstap_fit_project + kstap_detect (5 launches per tile, no
     overlap, FP32 bank); batched = one CUDA graph holding one autotuned batch
-    per (q, r_b) class on parallel branches, bank on the tensor cores
-    (`precision`).  The fits are bit-identical; T agrees to the 16-bit route's
-    bar (tested)."""
+    per (q, r_b) class on parallel branches, with the FP32 bank (batching
+    alone) and with the bank on the tensor cores (`precision`).  The fits are
+    bit-identical; T agrees to the 16-bit route's bar (tested)."""
     import torch
     import gen
     import paper_1604_03622_b300 as K
@@ -341,24 +341,30 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
     for i, w in enumerate(tiles):
         classes.setdefault((w.q, w.r_b), []).append(i)
     keys = sorted(classes)
-    ctxs, bctxs, descs, bufs, Ys = {}, {}, {}, {}, [None] * len(tiles)
+    Ys = [torch.from_numpy(f.Y).to(dev) for f in frames]
+    ctxs = {}
     for key in keys:
-        idx = classes[key]
-        w0, f0 = tiles[idx[0]], frames[idx[0]]
+        w0, f0 = tiles[classes[key][0]], frames[classes[key][0]]
         ctxs[key] = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev))
-        ks = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev), precision=precision)
-        bctxs[key] = ks
-        for i in idx:
-            Ys[i] = torch.from_numpy(frames[i].Y).to(dev)
-        # the descriptors hold raw device pointers: keep the tensors alive
-        bufs[key] = [ks.alloc_outputs(Ys[i].shape[1], Ys[i].shape[2]) for i in idx]
-        descs[key] = [ks.frame_desc(Ys[i], b) for i, b in zip(idx, bufs[key])]
     stream = torch.cuda.current_stream(dev)
-    tuning = {}
-    for key in keys:
-        t = K.kstap_autotune(bctxs[key].ctx, descs[key], reps=2)
-        tuning[f"q{key[0]}_r{key[1]}"] = dict(waves=t.waves, tc=t.tc, ms=round(t.ms_per_batch, 3))
-    graph = K.kstap_graph_create([bctxs[k].ctx for k in keys], [descs[k] for k in keys])
+
+    def make_graph(prec):
+        """Per-class contexts, output buffers, autotuned tuning and the graph."""
+        bctxs, bufs, descs, tuning = {}, {}, {}, {}
+        for key in keys:
+            idx = classes[key]
+            w0, f0 = tiles[idx[0]], frames[idx[0]]
+            ks = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev), precision=prec)
+            bctxs[key] = ks
+            # the descriptors hold raw device pointers: keep the tensors alive
+            bufs[key] = [ks.alloc_outputs(Ys[i].shape[1], Ys[i].shape[2]) for i in idx]
+            descs[key] = [ks.frame_desc(Ys[i], b) for i, b in zip(idx, bufs[key])]
+            t = K.kstap_autotune(ks.ctx, descs[key], reps=2)
+            tuning[f"q{key[0]}_r{key[1]}"] = dict(waves=t.waves, tc=t.tc,
+                                                  ms=round(t.ms_per_batch, 3))
+        graph = K.kstap_graph_create([bctxs[k].ctx for k in keys], [descs[k] for k in keys])
+        return bctxs, bufs, graph, tuning
+
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ncells = sum(w.cells for w in tiles)
 
@@ -382,19 +388,26 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
                 ks.run(Ys[i])
 
     plain_ms = timed(plain)
-    batched_ms = timed(lambda: K.kstap_graph_launch(graph, stream.cuda_stream))
-    K.kstap_graph_destroy(graph)
-    for ks in list(ctxs.values()) + list(bctxs.values()):
+    arms, tunings = {}, {}
+    for tag, prec in (("batched_fp32", "fp32"), ("batched", precision)):
+        bctxs, bufs, graph, tuning = make_graph(prec)
+        ms = timed(lambda: K.kstap_graph_launch(graph, stream.cuda_stream))
+        K.kstap_graph_destroy(graph)
+        for ks in bctxs.values():
+            ks.close()
+        m = sum(ms) / len(ms)
+        arms[tag] = dict(cells_per_s=ncells / (m / 1e3), ms_per_batch=m, p99_ms=sorted(ms)[-1],
+                         graph_launches=1, kernel_launches=5 * len(keys), precision=prec)
+        tunings[tag] = tuning
+    for ks in ctxs.values():
         ks.close()
-    pm, bm = sum(plain_ms) / len(plain_ms), sum(batched_ms) / len(batched_ms)
+    pm = sum(plain_ms) / len(plain_ms)
     return dict(workload="tiles256", tiles=len(tiles), cells=ncells, classes=len(keys),
                 plain=dict(cells_per_s=ncells / (pm / 1e3), ms_per_batch=pm,
                            p99_ms=sorted(plain_ms)[-1], kernel_launches=5 * len(tiles),
                            precision="fp32"),
-                batched=dict(cells_per_s=ncells / (bm / 1e3), ms_per_batch=bm,
-                             p99_ms=sorted(batched_ms)[-1], graph_launches=1,
-                             kernel_launches=5 * len(keys), precision=precision),
-                speedup=pm / bm, tuning=tuning)
+                **arms, speedup=pm / arms["batched"]["ms_per_batch"],
+                speedup_fp32=pm / arms["batched_fp32"]["ms_per_batch"], tuning=tunings)
 
 
 # --------------------------------------------------------- q = 32 frame ---
@@ -607,14 +620,16 @@ def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
 
 # ----------------------------------------------------------------- serving ---
 def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
-                batched_cfg=(16, 4, 1 << 20), extra_cfgs=()):
-    """Poisson stream of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
-    V = 64) at 0.8 x the measured plain capacity, through kstap_submit /
-    kstap_poll with a 120 GB HBM budget (60 GB per q class).  plain: one frame
-    at a time (batch 1, one stream, FP32 bank); batched: continuous batching
-    (batch <= 16 frames and <= 1 M cells, 4 streams, bank on the tensor cores).
-    Latency = completion - arrival.  extra_cfgs: more (max_batch, streams,
-    batch cells) configurations of the batched arm, reported under "extra"."""
+                batched_cfg=(16, 4, 1 << 20), loads=(0.8, 1.5)):
+    """Poisson streams of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
+    V = 64) through kstap_submit / kstap_poll with a 120 GB HBM budget (60 GB
+    per q class), at each load in `loads` x the measured plain capacity (0.8:
+    latency below saturation; 1.5: arrivals outpace service, so cells/s is the
+    service rate).  Arms on the same arrivals: plain (one frame at a time:
+    batch 1, one stream, FP32 bank), batched FP32 (continuous batching: batch
+    <= 16 frames and <= 1 M cells, 4 streams) and batched with the bank on the
+    tensor cores (`precision`), which separates batching from precision.
+    Latency = completion - arrival."""
     import threading
     import torch
     import gen
@@ -641,10 +656,9 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
             b.synchronize()
             per_frame_s.append(a.elapsed_time(b) / 1e3)
         ks.close()
-    rate = 0.8 / float(np.mean(per_frame_s))
-    t_arr, pick = gen.poisson_arrivals(n_requests, rate, len(pool))
+    capacity = 1.0 / float(np.mean(per_frame_s))
 
-    def run(max_batch, max_inflight, prec, cap=None):
+    def run(t_arr, pick, max_batch, max_inflight, prec, cap=None):
         ctxs = {}
         for q in qs:
             i0 = [i for i, w in enumerate(pool) if w.q == q][0]
@@ -657,7 +671,6 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
             ctxs[q] = ks
         tickets = [None] * n_requests
         t0 = time.perf_counter()
-        sub_us = [0.0] * n_requests
 
         def submitter():
             for k in range(n_requests):
@@ -667,11 +680,10 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
                 i = int(pick[k])
                 ks = ctxs[pool[i].q]
                 tickets[k] = (ks, K.kstap_submit(ks.ctx, Ys[i], Ys[i].shape[1], Ys[i].shape[2]))
-                sub_us[k] = (time.perf_counter() - t0) * 1e6
 
         th = threading.Thread(target=submitter)
         th.start()
-        lat, cells, t_end = [], 0, 0.0
+        lat, cells = [], 0
         for k in range(n_requests):
             while tickets[k] is None:
                 time.sleep(1e-4)
@@ -690,14 +702,19 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
                     mean_ms=float(np.mean(lat)), wall_s=t_end, max_batch=max_batch,
                     streams=max_inflight, precision=prec, batch_cells=cap)
 
-    plain = run(1, 1, "fp32")
-    batched = run(batched_cfg[0], batched_cfg[1], precision, batched_cfg[2])
-    extra = [run(mb, mi, precision, cap) for (mb, mi, cap) in extra_cfgs]
-    return dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
-                q=qs, r_b=3, V=64, budget_gb=120, arrival_rate_hz=rate,
-                plain_capacity_frames_per_s=1.0 / float(np.mean(per_frame_s)),
-                mean_cells_per_frame=float(np.mean([pool[int(i)].cells for i in pick])),
-                plain=plain, batched=batched, **({"extra": extra} if extra else {}))
+    out = dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
+               q=qs, r_b=3, V=64, budget_gb=120, plain_capacity_frames_per_s=capacity)
+    for load in loads:
+        t_arr, pick = gen.poisson_arrivals(n_requests, load * capacity, len(pool))
+        out[f"load_{load:g}"] = dict(
+            arrival_rate_hz=load * capacity,
+            mean_cells_per_frame=float(np.mean([pool[int(i)].cells for i in pick])),
+            plain=run(t_arr, pick, 1, 1, "fp32"),
+            batched_fp32=run(t_arr, pick, batched_cfg[0], batched_cfg[1], "fp32",
+                             batched_cfg[2]),
+            batched=run(t_arr, pick, batched_cfg[0], batched_cfg[1], precision,
+                        batched_cfg[2]))
+    return out
 
 
 # ------------------------------------------------------------------ main ----
@@ -864,6 +881,20 @@ def main():
                    kind="oracle", sample=f"{len(cells)} seeded random cells of the "
                                          f"{wl.H}x{wl.W} frame (FP64, OpenMP)")
 
+    # the metric's comparison, batched vs plain, from the batched and serving legs
+    bvp = {}
+    if batched:
+        bvp["tiles256_cells_per_s"] = dict(plain=batched["plain"]["cells_per_s"],
+                                           batched_fp32=batched["batched_fp32"]["cells_per_s"],
+                                           batched=batched["batched"]["cells_per_s"])
+    if serving:
+        for load, tag in (("load_1.5", "serving_saturated"), ("load_0.8", "serving_0.8_load")):
+            if load in serving:
+                arms = serving[load]
+                bvp[tag] = {a: dict(cells_per_s=arms[a]["cells_per_s"], p50_ms=arms[a]["p50_ms"],
+                                    p99_ms=arms[a]["p99_ms"])
+                            for a in ("plain", "batched_fp32", "batched")}
+
     lat = sorted(step_ms)
     line = dict(
         metric=METRIC, value=value, unit="cells/s", n_gpus=ws, steps=args.steps,
@@ -885,6 +916,7 @@ def main():
                                                   "stream during frame s"),
         gpu_launches=sum(v[1] for v in kt.values()),
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
+        batched_vs_plain=bvp or None,
         batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing,
         robustness=robustness, multipass=multipass)
     print(json.dumps(line), flush=True)

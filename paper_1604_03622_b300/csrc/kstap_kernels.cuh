@@ -927,6 +927,58 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
   for (int m = 0; m < P; ++m)
     if (m < ra) trA += d[m];
   const float sc = (trA != 0.f) ? (float)P / trA : 1.f;
+  if (g.filter == 1 && ra == 1) {
+    // classical filter (Sec. 5): its projector keeps the clutter orthogonal to
+    // u_a, so the statistic needs U_A beyond the single-precision flip-flop's
+    // ~1e-7.  One Alg. 2 update in FP64 from the final a: a~ = M a (M as
+    // accumulated), u_a = the leading eigenvector of herm(vec^-1 a~) by FP64
+    // power iteration from the single-precision one (the spatial eigenvalue
+    // ratio is ~0.1, so six steps take 1e-7 below double rounding).
+    double yr[PP], yi[PP];
+#pragma unroll
+    for (int J = 0; J < PP; ++J) {
+      double sr = 0.0, si = 0.0;
+#pragma unroll
+      for (int Jp = 0; Jp < PP; ++Jp) {
+        const float2 m = (J <= Jp) ? M[tri_idx(PP, J, Jp)] : cconj(M[tri_idx(PP, Jp, J)]);
+        sr += (double)m.x * a[Jp].x - (double)m.y * a[Jp].y;
+        si += (double)m.x * a[Jp].y + (double)m.y * a[Jp].x;
+      }
+      yr[J] = sr;
+      yi[J] = si;
+    }
+    double ur[P], ui[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      ur[i] = U[i][0].x;
+      ui[i] = U[i][0].y;
+    }
+    for (int step = 0; step < 6; ++step) {
+      double vr[P], vi[P], n2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        vr[i] = vi[i] = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < P; ++kk) {
+          // herm(vec^-1 y)[i][kk] = (y[i + P kk] + conj(y[kk + P i])) / 2
+          const double hr = 0.5 * (yr[i + P * kk] + yr[kk + P * i]);
+          const double hi = 0.5 * (yi[i + P * kk] - yi[kk + P * i]);
+          vr[i] += hr * ur[kk] - hi * ui[kk];
+          vi[i] += hr * ui[kk] + hi * ur[kk];
+        }
+        n2 += vr[i] * vr[i] + vi[i] * vi[i];
+      }
+      const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        ur[i] = vr[i] * inv;
+        vi[i] *= inv;
+        ui[i] = vi[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) U[i][0] = make_float2((float)ur[i], (float)ui[i]);
+  }
 #pragma unroll
   for (int i = 0; i < P; ++i)
 #pragma unroll
@@ -1951,7 +2003,17 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
         acc_ffxf(si, ci, C.z, C.w, u.x);
         acc_ffxf(si, ci, C.x, C.y, -u.y);
       }
-      const ff cre = ff_make(sr, cr), cim = ff_make(si, ci);
+      // c_m / |u_a|^2 (float-float): u_a is stored in single precision, so
+      // |u_a|^2 differs from 1 by ~1e-7, which would leave that fraction of
+      // u_a's clutter in E
+      float ns = 0.f, nc = 0.f;
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        acc_prod(ns, nc, Ua[k2].x, Ua[k2].x);
+        acc_prod(ns, nc, Ua[k2].y, Ua[k2].y);
+      }
+      const ff nu2 = ff_make(ns, nc);
+      const ff cre = ff_div(ff_make(sr, cr), nu2), cim = ff_div(ff_make(si, ci), nu2);
       const float4 C = Cs[i * R + m];
       const float2 u = Ua[i];
       float r1 = C.x, r2 = C.y, i1 = C.z, i2 = C.w;   // C[i][m] - u_a[i] c_m
