@@ -51,6 +51,9 @@ def parse():
                          "fp16x3 / bf16x3: tensor cores, hi + lo splits)")
     ap.add_argument("--cpu-sample", type=int, default=1024,
                     help="cells of the oracle CPU baseline sample")
+    ap.add_argument("--lag-store", type=int, default=1, choices=[0, 1],
+                    help="1: the moments pass writes the exact lag sums to a workspace store "
+                         "the B pass reads; 0: the B pass recomputes them (no store)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
@@ -746,6 +749,7 @@ def main():
     ks = KStap.from_workload(wl, frames[0].bank_a, frames[0].bank_b, device=str(dev),
                              precision=args.precision,
                              stream=stream)
+    K.kstap_set_tuning(ks.ctx, 4, 0, lag_store=args.lag_store)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ncell = wl.H * wl.W
 
@@ -902,6 +906,7 @@ def main():
         scaling="weak", vs_baseline=None, dtype="f32+ff/i64" + ("" if args.precision == "fp32" else "+" + args.precision),
         data="synthetic",
         config=dict(workload=wl.name, path="plain", precision=args.precision, cells_per_frame=ncell,
+                    lag_store=args.lag_store,
                     p=wl.p, q=wl.q,
                     r_a=wl.r_a, r_b=wl.r_b, n=wl.n, V=wl.V, cnr_db=wl.cnr_db,
                     l2="256 MiB flush between timed steps, outside the events",

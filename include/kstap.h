@@ -260,18 +260,23 @@ kstap_status kstap_graph_destroy(kstap_graph* graph);
 /* Launch tuning of a context.  waves: persistent grid size in multiples of
  * (SMs x resident CTAs), 1..64; tc: cells per tile of the B / U_B pass
  * (0 = default: 32, or 16 at q = 32; allowed 8, 16, 32 with tc = 32 only for
- * q <= 16).  Tuning changes only the schedule, not the arithmetic of any
- * cell. */
+ * q <= 16); lag_store: 1 = the moments pass writes the exact lag sums to a
+ * workspace store that the B pass reads (9 q (W + q - 1) x 16 B per cell row,
+ * e.g. 2.4 GB for a 1024^2 frame at q = 16), 0 = the B pass recomputes them
+ * from its frame tile and the store is not allocated (p = 3 only; stacked
+ * passes need the store).  Tuning changes only the schedule and memory, not
+ * the arithmetic of any cell: results are bit-identical. */
 typedef struct {
   int waves;
   int tc;
+  int lag_store;
   float ms_per_batch; /* measured by kstap_autotune */
 } kstap_tuning;
 
 /* Autotuner: times kstap_run_batch on these frames (reps repetitions after a
  * warm-up) for every candidate (waves in {1,2,4,8,16}) x (tc in {16,32}, or
- * {8,16} at q = 32), keeps the fastest in the context and reports it.
- * Synchronises the context stream. */
+ * {8,16} at q = 32) x (lag_store in {1, 0} for p = 3), keeps the fastest in
+ * the context and reports it.  Synchronises the context stream. */
 kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, int reps,
                             kstap_tuning* out);
 kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* tuning);

@@ -50,7 +50,8 @@ class KstapFrame(ctypes.Structure):
 
 
 class KstapTuning(ctypes.Structure):
-    _fields_ = [("waves", ctypes.c_int), ("tc", ctypes.c_int), ("ms_per_batch", ctypes.c_float)]
+    _fields_ = [("waves", ctypes.c_int), ("tc", ctypes.c_int), ("lag_store", ctypes.c_int),
+                ("ms_per_batch", ctypes.c_float)]
 
 
 class KstapResult(ctypes.Structure):
@@ -304,8 +305,8 @@ def kstap_autotune(ctx: int, frames, reps: int = 3) -> KstapTuning:
     return t
 
 
-def kstap_set_tuning(ctx: int, waves: int, tc: int = 0) -> None:
-    t = KstapTuning(waves, tc, 0.0)
+def kstap_set_tuning(ctx: int, waves: int, tc: int = 0, lag_store: int = 1) -> None:
+    t = KstapTuning(waves, tc, lag_store, 0.0)
     _check(lib().kstap_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 

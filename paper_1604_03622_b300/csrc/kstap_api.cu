@@ -374,6 +374,10 @@ bool smem_fits(const Geom& g, bool lag_store, std::string& why) {
   return true;
 }
 
+// Whether this context's fits write the lag store (stacked passes always do:
+// k_mgram reads it).
+bool store_lags(const kstap_ctx* ctx) { return ctx->prm.p > 3 || ctx->tune.lag_store != 0; }
+
 kstap_status dispatch_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                           char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
                           cudaStream_t s) {
@@ -465,7 +469,7 @@ kstap_status enqueue_batch(kstap_ctx* ctx, kstap_ctx* prof, const std::vector<Fr
   if (fr.size() > 1) JL.table = jobs_dev;
   JL.report = report;
   JL.fault = ctx->fault;
-  kstap_status st = dispatch_fit(ctx, prof, g, JL, scratch, L, true, ctx->sm_count,
+  kstap_status st = dispatch_fit(ctx, prof, g, JL, scratch, L, store_lags(ctx), ctx->sm_count,
                                  ctx->tune.waves, s);
   if (st != KSTAP_OK) return st;
   return dispatch_detect(ctx, prof, g, JL, ctx->sm_count, ctx->tune.waves, s);
@@ -607,12 +611,13 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
   // A frame whose workspace exceeds the budget runs as row strips, one after
   // the other on the stream, in one strip-sized workspace.
   int rows = H;
-  const size_t full = make_layout(p, {{H, W}}, true).total;
+  const bool store = store_lags(ctx);
+  const size_t full = make_layout(p, {{H, W}}, store).total;
   if (ctx->budget && full > ctx->budget) {
-    const size_t per_row = std::max<size_t>(1, make_layout(p, {{1, W}}, true).total);
+    const size_t per_row = std::max<size_t>(1, make_layout(p, {{1, W}}, store).total);
     rows = (int)std::max<size_t>(kstap::kMomRows, ctx->budget / per_row);
     rows -= rows % kstap::kMomRows;
-    if (make_layout(p, {{std::min(rows, H), W}}, true).total > ctx->budget)
+    if (make_layout(p, {{std::min(rows, H), W}}, store).total > ctx->budget)
       return fail(ctx, KSTAP_ENOMEM, "a %d-row strip of this frame exceeds the HBM budget %zu B",
                   kstap::kMomRows, ctx->budget);
   }
@@ -621,7 +626,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
   KSTAP_CUDA(ctx, cudaMemsetAsync(ctx->report, 0, kReportCounters * sizeof(unsigned long long), ctx->stream));
   for (const Frame& s : strips) {
     const int sh = s.H_in - 2 * p.ring_r;
-    const Layout L = make_layout(p, {{sh, W}}, true);
+    const Layout L = make_layout(p, {{sh, W}}, store);
     st = ensure_ws(ctx, L.total);
     if (st != KSTAP_OK) return st;
     std::vector<Frame> fr{s};
@@ -630,7 +635,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
     fill_jobs(p, g, fr, (char*)ctx->ws, &L, jobs, JL);
     JL.report = ctx->report;
     JL.fault = ctx->fault;
-    st = dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, true, ctx->sm_count, ctx->tune.waves,
+    st = dispatch_fit(ctx, ctx, g, JL, (char*)ctx->ws, L, store, ctx->sm_count, ctx->tune.waves,
                       ctx->stream);
     if (st != KSTAP_OK) return st;
   }
@@ -664,7 +669,7 @@ kstap_status kstap_run_batch(kstap_ctx* ctx, const kstap_frame* frames, int n) {
   std::vector<std::pair<int, int>> HW;
   kstap_status st = frames_from(ctx, frames, n, fr, HW);
   if (st != KSTAP_OK) return st;
-  const Layout L = make_layout(ctx->prm, HW, true);
+  const Layout L = make_layout(ctx->prm, HW, store_lags(ctx));
   st = ensure_ws(ctx, L.total);
   if (st != KSTAP_OK) return st;
   if (n > 1) {
@@ -727,7 +732,7 @@ kstap_status kstap_graph_create(kstap_ctx* const* ctxs, const kstap_frame* const
     std::vector<std::pair<int, int>> HW;
     kstap_status st = frames_from(ctx, frames[c], nframes[c], plans[c].fr, HW);
     if (st != KSTAP_OK) return bail(fail(nullptr, st, "context %d: %s", c, ctx->err.c_str()));
-    plans[c].L = make_layout(ctx->prm, HW, true);
+    plans[c].L = make_layout(ctx->prm, HW, store_lags(ctx));
     void* ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, plans[c].L.total);
     if (e != cudaSuccess)
@@ -822,16 +827,23 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   const std::vector<int> tcs =
       (ctx->prm.q >= 32) ? std::vector<int>{8, 16} : std::vector<int>{16, 32};
   const int wavesv[] = {1, 2, 4, 8, 16};
+  std::vector<int> stores{1};
+  if (ctx->prm.p <= 3) stores.push_back(0);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best = 1e30f;
   Tuning bt = saved;
   kstap_status st = KSTAP_OK;
+  for (size_t li = 0; li < stores.size() && st == KSTAP_OK; ++li)
   for (int tc : tcs) {
+    const int ls = stores[li];
+    std::string why;
+    if (!ls && !smem_fits(make_geom(ctx->prm, ctx->V, tc), false, why)) continue;
     for (int w : wavesv) {
       ctx->tune.tc = tc;
       ctx->tune.waves = w;
+      ctx->tune.lag_store = ls;
       st = kstap_run_batch(ctx, frames, n);   // warm-up (and workspace growth)
       if (st != KSTAP_OK) break;
       cudaEventRecord(a, ctx->stream);
@@ -859,6 +871,7 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   if (out) {
     out->waves = bt.waves;
     out->tc = bt.tc > 0 ? bt.tc : ((ctx->prm.q >= 32) ? 16 : kstap::kTileCells);
+    out->lag_store = bt.lag_store;
     out->ms_per_batch = best;
   }
   return KSTAP_OK;
@@ -871,8 +884,16 @@ kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* t) {
     return fail(ctx, KSTAP_EINVAL, "tc must be 0, 8, 16 or 32");
   if (t->tc == 32 && ctx->prm.q >= 32)
     return fail(ctx, KSTAP_EINVAL, "tc = 32 does not fit shared memory at q = 32");
+  if (t->lag_store != 0 && t->lag_store != 1)
+    return fail(ctx, KSTAP_EINVAL, "lag_store must be 0 or 1");
+  if (!t->lag_store && ctx->prm.p > 3)
+    return fail(ctx, KSTAP_EINVAL, "stacked passes (p > 3) need the lag store");
+  std::string why;
+  if (!t->lag_store && !smem_fits(make_geom(ctx->prm, ctx->V, t->tc), false, why))
+    return fail(ctx, KSTAP_EINVAL, "%s", why.c_str());
   ctx->tune.waves = t->waves;
   ctx->tune.tc = t->tc;
+  ctx->tune.lag_store = t->lag_store;
   return KSTAP_OK;
 }
 
@@ -1063,7 +1084,7 @@ void launch_batch(Server* s, const std::vector<std::pair<uint64_t, int>>& items)
     fbytes += up256(factor_bytes(p, (size_t)H * W));
     if (host[k]) ybytes += up256((size_t)p.p * fr[k].H_in * fr[k].W_in * sizeof(kstap_c64));
   }
-  const Layout L = make_layout(p, HW, true);
+  const Layout L = make_layout(p, HW, store_lags(ctx));
   const size_t total = up256(L.total) + fbytes + ybytes + up256(fr.size() * sizeof(Job));
   char* mem = nullptr;
   kstap_status status = KSTAP_OK;
@@ -1276,7 +1297,7 @@ kstap_status kstap_submit(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int W_in
   const size_t cells = (size_t)r.H * r.W;
   r.out_bytes = up256(cells * 4) * 2 + up256(cells);
   auto part_scratch = [&](int rows) {
-    return make_layout(p, {{rows, r.W}}, true).total + factor_bytes(p, (size_t)rows * r.W) +
+    return make_layout(p, {{rows, r.W}}, store_lags(ctx)).total + factor_bytes(p, (size_t)rows * r.W) +
            (r.on_host ? (size_t)p.p * (rows + 2 * p.ring_r) * W_in * sizeof(kstap_c64) : 0) +
            4096;
   };

@@ -28,6 +28,7 @@ namespace kh {
 struct Tuning {
   int waves = 4;   // persistent grid = SMs x resident CTAs x waves (capped by tiles)
   int tc = 0;      // cells per tile in the B pass (0 = default: 32, or 16 for q = 32)
+  int lag_store = 1;   // 1: the moments pass writes the lag store; 0: the B pass recomputes
 };
 }  // namespace kh
 

@@ -104,3 +104,32 @@ def test_autotune_picks_a_candidate_and_keeps_results():
         for k in KEYS:
             assert np.array_equal(got[k], r[k]), k
     ks.close()
+
+
+@pytest.mark.parametrize("name,sizes", [("small64", [(20, 45), (9, 70)]),
+                                        ("frame1024", [(7, 40), (33, 29), (1, 1)]),
+                                        ("precision2048", [(6, 40), (11, 17)])])
+def test_recomputed_lags_bit_identical_to_lag_store(name, sizes):
+    """lag_store = 0 (the B pass recomputes the exact lag sums from its frame
+    tile, no store in the workspace) gives the same bits as the store, per
+    frame and in a batch: the sums are exact integers either way."""
+    import torch
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    frames = _frames(name, sizes)
+    ks = KStap.from_workload(frames[0].wl, frames[0].bank_a, frames[0].bank_b)
+    Ys = [torch.from_numpy(f.Y).cuda() for f in frames]
+    ref = [_np(ks.run(Y, T_all=True)) for Y in Ys]
+    K.kstap_set_tuning(ks.ctx, 4, 0, lag_store=0)
+    for r, Y in zip(ref, Ys):
+        got = _np(ks.run(Y, T_all=True))
+        for k in KEYS:
+            assert np.array_equal(got[k], r[k]), ("per frame", k)
+    bufs = [ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
+    K.kstap_run_batch(ks.ctx, [ks.frame_desc(Y, b) for Y, b in zip(Ys, bufs)])
+    torch.cuda.synchronize()
+    for r, b in zip(ref, bufs):
+        got = _np(b)
+        for k in KEYS:
+            assert np.array_equal(got[k], r[k]), ("batch", k)
+    ks.close()
