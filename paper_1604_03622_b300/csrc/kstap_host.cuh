@@ -166,8 +166,9 @@ inline size_t smem_detect(const Geom& g) {
   const size_t CS = 2 * (size_t)P * Q + 2 * (size_t)Q * R + 2 * P + 4 * (size_t)P * R;
   const size_t cells = cells_per_detect_block(Q);
   const size_t QS = std::max(R, P + 1);   // near-blind queue entry (float2) per pair
+  const size_t PF = (size_t)P * Q + 2 * (size_t)Q * R + 2 * P;   // prefetch buffer per cell
   return (size_t)(P + Q) * V * 8 + 2 * (size_t)V * 4 + cells * CS * 8 +
-         (kstap::kThreads / 32) * kstap::kBlindQ * (QS * 8 + 4);
+         (kstap::kThreads / 32) * kstap::kBlindQ * (QS * 8 + 4) + cells * PF * 8;
 }
 
 // Largest dynamic shared memory a CTA may opt into on sm_103a (227 KB).

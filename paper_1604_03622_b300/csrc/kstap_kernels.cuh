@@ -767,6 +767,81 @@ __device__ void jacobi_small(float2 (&A)[N][N], float (&d)[N], float2 (&U)[N][N]
   }
 }
 
+// Classical filter (Sec. 5): its projector keeps the clutter orthogonal to
+// u_a, so the statistic needs U_A beyond the single-precision flip-flop's
+// ~1e-7.  After the flip-flop, one Alg. 2 update in FP64 from the final a (a
+// thread per cell): a~ = M a (M as accumulated), u_a = the leading
+// eigenvector of herm(vec^-1 a~) by FP64 power iteration from the
+// single-precision U_A (the spatial eigenvalue ratio is ~0.1, so six steps
+// take 1e-7 below double rounding).  A kernel of its own, launched for that
+// filter only, so the FP64 registers stay out of the flip-flop.
+template <int P>
+__global__ void __launch_bounds__(128)
+k_refine_ua(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __restrict__ aw) {
+  constexpr int PP = P * P;
+  constexpr int NE = PP * (PP + 1) / 2;
+  const size_t ncell = (size_t)JL.NC;
+  for (int tile = blockIdx.x; tile < JL.ntiles[kKindFlip]; tile += gridDim.x) {
+  int lt;
+  const Job& JB = job_of(JL, kKindFlip, tile, lt);
+  const size_t local = (size_t)lt * blockDim.x + threadIdx.x;
+  if (local >= (size_t)JB.H * JB.W) continue;
+  const size_t cell = (size_t)JB.cell0 + local;
+  float2 M[NE], a[PP];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) M[e] = Mw[e * ncell + cell];
+#pragma unroll
+  for (int J = 0; J < PP; ++J) a[J] = aw[J * ncell + cell];
+  float2 u[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) u[i] = JB.UA[local * P + i];
+  double yr[PP], yi[PP];
+#pragma unroll
+  for (int J = 0; J < PP; ++J) {
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int Jp = 0; Jp < PP; ++Jp) {
+      const float2 m = (J <= Jp) ? M[tri_idx(PP, J, Jp)] : cconj(M[tri_idx(PP, Jp, J)]);
+      sr += (double)m.x * a[Jp].x - (double)m.y * a[Jp].y;
+      si += (double)m.x * a[Jp].y + (double)m.y * a[Jp].x;
+    }
+    yr[J] = sr;
+    yi[J] = si;
+  }
+  double ur[P], ui[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    ur[i] = u[i].x;
+    ui[i] = u[i].y;
+  }
+  for (int step = 0; step < 6; ++step) {
+    double vr[P], vi[P], n2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      vr[i] = vi[i] = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < P; ++kk) {
+        // herm(vec^-1 y)[i][kk] = (y[i + P kk] + conj(y[kk + P i])) / 2
+        const double hr = 0.5 * (yr[i + P * kk] + yr[kk + P * i]);
+        const double hi = 0.5 * (yi[i + P * kk] - yi[kk + P * i]);
+        vr[i] += hr * ur[kk] - hi * ui[kk];
+        vi[i] += hr * ui[kk] + hi * ur[kk];
+      }
+      n2 += vr[i] * vr[i] + vi[i] * vi[i];
+    }
+    const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      ur[i] = vr[i] * inv;
+      vi[i] *= inv;
+      ui[i] = vi[i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < P; ++i) JB.UA[local * P + i] = make_float2((float)ur[i], (float)ui[i]);
+  }  // tile loop
+}
+
 // ------------------------------------------------ K2: flip-flop ------------
 // One thread per cell: Alg. 2 on M = R R^H.  Writes a = vec(A^) (FP32),
 // U_A, lamA (tr A^ = p), iterations and eta.
@@ -927,58 +1002,6 @@ k_flipflop(Geom g0, JobList JL, const float2* __restrict__ Mw, const float2* __r
   for (int m = 0; m < P; ++m)
     if (m < ra) trA += d[m];
   const float sc = (trA != 0.f) ? (float)P / trA : 1.f;
-  if (g.filter == 1 && ra == 1) {
-    // classical filter (Sec. 5): its projector keeps the clutter orthogonal to
-    // u_a, so the statistic needs U_A beyond the single-precision flip-flop's
-    // ~1e-7.  One Alg. 2 update in FP64 from the final a: a~ = M a (M as
-    // accumulated), u_a = the leading eigenvector of herm(vec^-1 a~) by FP64
-    // power iteration from the single-precision one (the spatial eigenvalue
-    // ratio is ~0.1, so six steps take 1e-7 below double rounding).
-    double yr[PP], yi[PP];
-#pragma unroll
-    for (int J = 0; J < PP; ++J) {
-      double sr = 0.0, si = 0.0;
-#pragma unroll
-      for (int Jp = 0; Jp < PP; ++Jp) {
-        const float2 m = (J <= Jp) ? M[tri_idx(PP, J, Jp)] : cconj(M[tri_idx(PP, Jp, J)]);
-        sr += (double)m.x * a[Jp].x - (double)m.y * a[Jp].y;
-        si += (double)m.x * a[Jp].y + (double)m.y * a[Jp].x;
-      }
-      yr[J] = sr;
-      yi[J] = si;
-    }
-    double ur[P], ui[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      ur[i] = U[i][0].x;
-      ui[i] = U[i][0].y;
-    }
-    for (int step = 0; step < 6; ++step) {
-      double vr[P], vi[P], n2 = 0.0;
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        vr[i] = vi[i] = 0.0;
-#pragma unroll
-        for (int kk = 0; kk < P; ++kk) {
-          // herm(vec^-1 y)[i][kk] = (y[i + P kk] + conj(y[kk + P i])) / 2
-          const double hr = 0.5 * (yr[i + P * kk] + yr[kk + P * i]);
-          const double hi = 0.5 * (yi[i + P * kk] - yi[kk + P * i]);
-          vr[i] += hr * ur[kk] - hi * ui[kk];
-          vi[i] += hr * ui[kk] + hi * ur[kk];
-        }
-        n2 += vr[i] * vr[i] + vi[i] * vi[i];
-      }
-      const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        ur[i] = vr[i] * inv;
-        vi[i] *= inv;
-        ui[i] = vi[i];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < P; ++i) U[i][0] = make_float2((float)ur[i], (float)ui[i]);
-  }
 #pragma unroll
   for (int i = 0; i < P; ++i)
 #pragma unroll
@@ -1660,6 +1683,11 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
                "r"(valid ? 16 : 0)
                : "memory");
 }
+// 8-byte asynchronous global -> shared copy (one complex64 sample).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -1924,6 +1952,10 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   constexpr int QS = (R > P + 1) ? R : P + 1;
   float2* qd_all = scr + CPB * CS;                                  // [warps][kBlindQ][QS]
   int* qi_all = reinterpret_cast<int*>(qd_all + (kThreads / 32) * kBlindQ * QS);
+  // per-slot prefetch buffer of the next tile's inputs: X [P][Q], U_B hi and
+  // lo [Q][R], U_A [P][RA] (2P slots)
+  constexpr int PF = P * Q + 2 * Q * R + 2 * P;
+  float2* pf_all = reinterpret_cast<float2*>(qi_all + (kThreads / 32) * kBlindQ);
   for (int i = threadIdx.x; i < P * V; i += blockDim.x) aT[i] = bank_aT[i];
   for (int i = threadIdx.x; i < Q * V; i += blockDim.x) bT[i] = bank_bT[i];
   for (int i = threadIdx.x; i < 2 * V; i += blockDim.x) na[i] = bank_n2[i];
@@ -1931,14 +1963,39 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / G, gl = lane % G;
   const int slot = warp * CPW + sub;
+  float2* pf = pf_all + slot * PF;
+  // the group of slot `slot` prefetches its cell of tile t (X, U_B hi / lo,
+  // U_A) with 8-byte cp.async into its own buffer while the CTA works on the
+  // previous tile; every lane copies exactly the elements it later reads
+  // back, so a wait on its own copies and a warp barrier order the data
+  auto prefetch = [&](int t) {
+    if (t < JL.ntiles[kKindDetect]) {
+      int ltn;
+      const Job& JN = job_of(JL, kKindDetect, t, ltn);
+      const size_t cn = (size_t)ltn * CPB + slot;
+      if (cn < (size_t)JN.H * JN.W) {
+        const int r = (int)(cn / JN.W), c = (int)(cn % JN.W);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+          cp_async8(pf + i * Q + gl, JN.Y + (size_t)i * JN.ch_stride +
+                                         (size_t)(r + g0.Rr) * JN.W_in + (c + g0.Ra + gl));
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          cp_async8(pf + P * Q + gl * R + m, JN.UBh + (cn * Q + gl) * R + m);
+          cp_async8(pf + P * Q + Q * R + gl * R + m, JN.UBl + (cn * Q + gl) * R + m);
+        }
+        for (int e = gl; e < P * RA; e += G)
+          cp_async8(pf + P * Q + 2 * Q * R + e, JN.UA + cn * P * RA + e);
+      }
+    }
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindDetect]; tile += gridDim.x) {
   int lt;
   const Job& JB = job_of(JL, kKindDetect, tile, lt);
   const Geom g = with_job(g0, JB);
   const float2* __restrict__ Y = JB.Y;
-  const float2* __restrict__ UA = JB.UA;
-  const float2* __restrict__ UBh = JB.UBh;
-  const float2* __restrict__ UBl = JB.UBl;
   float* __restrict__ T_all = JB.T_all;
   const size_t cell = (size_t)lt * CPB + slot;
   const size_t ncell = (size_t)g.H * g.W;
@@ -1951,20 +2008,19 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float2* Ua = Ul + Q * R;             // [P][RA] (2P slots)
   float4* Cs = reinterpret_cast<float4*>(Ua + 2 * P);   // [P][R] float-float complex
   float4* Es = Cs + P * R;                               // [P][R] F_A C, float-float (classical)
+  cp_async_wait<0>();
   if (live) {
-    const int r = (int)(cell / g.W), c = (int)(cell % g.W);
 #pragma unroll
-    for (int i = 0; i < P; ++i)
-      Xs[i * Q + gl] =
-          __ldg(Y + (size_t)i * g.ch_stride + (size_t)(r + g.Rr) * g.W_in + (c + g.Ra + gl));
+    for (int i = 0; i < P; ++i) Xs[i * Q + gl] = pf[i * Q + gl];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      Uh[gl * R + m] = UBh[(cell * Q + gl) * R + m];
-      Ul[gl * R + m] = UBl[(cell * Q + gl) * R + m];
+      Uh[gl * R + m] = pf[P * Q + gl * R + m];
+      Ul[gl * R + m] = pf[P * Q + Q * R + gl * R + m];
     }
-    for (int e = gl; e < P * RA; e += G) Ua[e] = UA[cell * P * RA + e];   // [i][m]
+    for (int e = gl; e < P * RA; e += G) Ua[e] = pf[P * Q + 2 * Q * R + e];   // [i][m]
   }
   __syncwarp();
+  prefetch(tile + gridDim.x);
   // C[i][m] = sum_j X[i][j] conj(U[j][m]), float-float
   if (live) {
     for (int it = gl; it < P * R; it += G) {

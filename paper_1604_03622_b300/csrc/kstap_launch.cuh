@@ -36,6 +36,9 @@ kstap_status enqueue_fit(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const J
     prof_collect(prof, KSTAP_K_FLIPFLOP);
     prof_begin(prof, KSTAP_K_FLIPFLOP, s);
     kstap::k_flipflop<P><<<g2, 128, 0, s>>>(g, JL, Mw, Sw, aw);
+    // the classical filter refines u_a in FP64 (counted with the flip-flop)
+    if (g.filter == KSTAP_FILTER_CLASSICAL && g.r_a == 1)
+      kstap::k_refine_ua<P><<<g2, 128, 0, s>>>(g, JL, Mw, aw);
     prof_end(prof, KSTAP_K_FLIPFLOP, s);
     KSTAP_CUDA(ctx, cudaGetLastError());
   } else {
