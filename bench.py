@@ -327,13 +327,26 @@ def measured_traffic(workload: str, precision: str, kernel: str, key: str = "byt
 
 
 # ------------------------------------------------------- batched vs plain ---
-def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
+def class_precision(precision: str, q: int) -> str:
+    """Bank arithmetic of one (q, r_b) class: "mixed" takes the tensor-core
+    FP16X3 bank at q = 32, where it is faster (32.7 against 49.1 ms on a 2048^2
+    frame), and the FP32 bank below, where the packed CUDA-core bank wins."""
+    if precision == "mixed":
+        return "fp16x3" if q >= 32 else "fp32"
+    return precision
+
+
+MIXED = "mixed (FP16X3 bank at q = 32, FP32 below)"
+
+
+def batched_leg(dev, steps: int, warmup: int, precision: str = "mixed"):
     """256 uneven tiles (q in {8,16,32}, r_b in {2,3,4}): plain = one tile at a
     time through kstap_fit_project + kstap_detect (5 launches per tile, no
     overlap, FP32 bank); batched = one CUDA graph holding one autotuned batch
     per (q, r_b) class on parallel branches, with the FP32 bank (batching
-    alone) and with the bank on the tensor cores (`precision`).  The fits are
-    bit-identical; T agrees to the 16-bit route's bar (tested)."""
+    alone) and with `precision` (default: the tensor-core bank at q = 32, FP32
+    below).  The fits are bit-identical; T agrees to the 16-bit route's bar
+    (tested)."""
     import torch
     import gen
     import paper_1604_03622_b300 as K
@@ -357,7 +370,8 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
         for key in keys:
             idx = classes[key]
             w0, f0 = tiles[idx[0]], frames[idx[0]]
-            ks = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev), precision=prec)
+            ks = KStap.from_workload(w0, f0.bank_a, f0.bank_b, device=str(dev),
+                                     precision=class_precision(prec, key[0]))
             bctxs[key] = ks
             # the descriptors hold raw device pointers: keep the tensors alive
             bufs[key] = [ks.alloc_outputs(Ys[i].shape[1], Ys[i].shape[2]) for i in idx]
@@ -400,7 +414,8 @@ def batched_leg(dev, steps: int, warmup: int, precision: str = "fp16x3"):
             ks.close()
         m = sum(ms) / len(ms)
         arms[tag] = dict(cells_per_s=ncells / (m / 1e3), ms_per_batch=m, p99_ms=sorted(ms)[-1],
-                         graph_launches=1, kernel_launches=5 * len(keys), precision=prec)
+                         graph_launches=1, kernel_launches=5 * len(keys),
+                         precision=MIXED if prec == "mixed" else prec)
         tunings[tag] = tuning
     for ks in ctxs.values():
         ks.close()
@@ -622,7 +637,7 @@ def paper_timing_leg(dev, reps: int = 5, cpu: bool = True):
 
 
 # ----------------------------------------------------------------- serving ---
-def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
+def serving_leg(dev, n_requests: int, precision: str = "mixed",
                 batched_cfg=(16, 4, 1 << 20), loads=(0.8, 1.5)):
     """Poisson streams of frames (sides U{256..4096}, q in {16, 32}, r_b = 3,
     V = 64) through kstap_submit / kstap_poll with a 120 GB HBM budget (60 GB
@@ -630,8 +645,9 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
     latency below saturation; 1.5: arrivals outpace service, so cells/s is the
     service rate).  Arms on the same arrivals: plain (one frame at a time:
     batch 1, one stream, FP32 bank), batched FP32 (continuous batching: batch
-    <= 16 frames and <= 1 M cells, 4 streams) and batched with the bank on the
-    tensor cores (`precision`), which separates batching from precision.
+    <= 16 frames and <= 1 M cells, 4 streams) and batched with `precision`
+    (default: the tensor-core bank at q = 32, FP32 below), which separates
+    batching from precision.
     Latency = completion - arrival."""
     import threading
     import torch
@@ -667,7 +683,7 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
             i0 = [i for i, w in enumerate(pool) if w.q == q][0]
             ks = KStap.from_workload(pool[i0], frames[i0].bank_a, frames[i0].bank_b,
                                      device=str(dev), hbm_budget_bytes=budget // len(qs),
-                                     precision=prec)
+                                     precision=class_precision(prec, q))
             K.kstap_serve_config(ks.ctx, max_batch, max_inflight)
             if cap is not None:
                 K.kstap_serve_batch_cells(ks.ctx, cap)
@@ -703,7 +719,8 @@ def serving_leg(dev, n_requests: int, precision: str = "fp16x3",
         return dict(cells_per_s=cells / t_end, p50_ms=lat[len(lat) // 2],
                     p99_ms=lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                     mean_ms=float(np.mean(lat)), wall_s=t_end, max_batch=max_batch,
-                    streams=max_inflight, precision=prec, batch_cells=cap)
+                    streams=max_inflight, precision=MIXED if prec == "mixed" else prec,
+                    batch_cells=cap)
 
     out = dict(workload="serving_stream", requests=n_requests, pool_frames=len(pool),
                q=qs, r_b=3, V=64, budget_gb=120, plain_capacity_frames_per_s=capacity)
