@@ -122,7 +122,8 @@ class Workload:
 
 # Training geometry per n = 2pq (p = 3): a centred range x azimuth box minus a
 # centred guard box, (ring_r, ring_a, guard_r, guard_a).
-RING_FOR_N = {48: (3, 4, 1, 2), 96: (3, 7, 1, 1), 120: (4, 7, 1, 2), 192: (4, 11, 1, 2)}
+RING_FOR_N = {48: (3, 4, 1, 2), 72: (4, 4, 1, 1), 96: (3, 7, 1, 1), 120: (4, 7, 1, 2),
+              144: (4, 8, 1, 1), 192: (4, 11, 1, 2)}
 
 
 def make_workload(name, H, W, q, r_b, n, V, cnr_db, n_targets, snr_db, seed_off, p=3, r_a=1):
@@ -143,6 +144,11 @@ WORKLOADS: Dict[str, Workload] = {
     # 2048x2048 cells, q=32, r_b=4, n=192 (9x23 minus 3x5), V=128, 40 dB CNR.
     "precision2048": make_workload("precision2048", 2048, 2048, 32, 4, 192, 128, 40.0, 200,
                                    (0.0, 15.0), 3),
+    # the windows between the configurations' q values: q = 12 (n = 72, the
+    # literal 9x9 box minus 3x3 guard) and q = 24 (n = 144, 9x17 minus 3x3),
+    # 256x256 cells, 40 dB CNR, targets at the 1024^2 frame's density
+    "frame_q12": make_workload("frame_q12", 256, 256, 12, 3, 72, 48, 40.0, 13, (0.0, 15.0), 7),
+    "frame_q24": make_workload("frame_q24", 256, 256, 24, 4, 144, 96, 40.0, 13, (0.0, 15.0), 8),
 }
 
 

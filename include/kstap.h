@@ -62,15 +62,17 @@ typedef enum {
 /* Model and detector parameters.  Notation of the paper: p channels, q
  * pulses (azimuth window), ranks r_a, r_b of A and B (Eq. SparseOpt), Alg. 2
  * tolerance eps and iteration cap, detection threshold tau on Tmax.
- * Limits of this build: p == 3 with q in {8, 16, 32} and r_a == 1 (the
- * paper's rank-one spatial model, Eq. KronCov) or r_a == 2 (KSTAP_FP32 bank
- * and Kron-STAP filter); or p == 6 -- K = 2 registered passes of 3 channels
- * stacked as one frame (Sec. 3), spatial rank r_a in {1, 2} -- with q in
- * {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
- * 1 <= r_b <= 4 with r_b < q (Sec. 5 warns against r_b close to q),
- * ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1) <= 1024, and a
- * training box whose tiles fit shared memory.  Other values give
- * KSTAP_EINVAL. */
+ * Limits of this build: p == 3 with q in {8, 12, 16, 24, 32} and r_a == 1
+ * (the paper's rank-one spatial model, Eq. KronCov) or r_a == 2 (KSTAP_FP32
+ * bank and Kron-STAP filter); or p == 6 -- K = 2 registered passes of 3
+ * channels stacked as one frame (Sec. 3), spatial rank r_a in {1, 2} -- with
+ * q in {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
+ * 1 <= r_b <= min(q - 1, 8) (Sec. 5 warns against r_b close to q); r_b > 4
+ * needs p == 3 and the KSTAP_FP32 bank, and every cell's U_B then comes from
+ * block subspace iteration with an FP64 Rayleigh-Ritz step (slower than the
+ * r_b <= 4 path).  ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1)
+ * <= 1024, and a training box whose tiles fit shared memory.  Other values
+ * give KSTAP_EINVAL. */
 typedef struct {
   int p, q, r_a, r_b;
   int ring_r, ring_a, guard_r, guard_a;
@@ -149,9 +151,10 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
  * ill-gapped path: their leading r_b eigenvalues of B were not separated
  * from the next one well enough for subspace iteration on r_b vectors (the
  * rate estimate left more than ~2e-7 of subspace error after 4 steps), so
- * U_B and lambda_B were recomputed by block subspace iteration on min(q, 8)
- * vectors with a Rayleigh-Ritz step solved by FP64 Jacobi sweeps.  Any
- * pointer may be NULL.  Returns KSTAP_WARN_NOCONV if any cell stopped at
+ * U_B and lambda_B were recomputed by block subspace iteration on
+ * min(q, max(8, r_b + 4)) vectors with a Rayleigh-Ritz step solved by FP64
+ * Jacobi sweeps.  With r_b > 4 every cell takes that path and eig_refined
+ * stays 0.  Any pointer may be NULL.  Returns KSTAP_WARN_NOCONV if any cell stopped at
  * max_iter (its factors are the last iterate, valid but not converged to
  * eps), else KSTAP_OK. */
 kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite,

@@ -21,7 +21,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17"] + ARCH + ["-lineinfo", "-Xcompiler", "-fPIC",
                                              "-diag-suppress", "177"]
 # (p, q) classes with their own translation units; must match KSTAP_CLASSES in
 # csrc/kstap_host.cuh
-CLASSES = [(3, 8), (3, 16), (3, 32), (6, 8), (6, 16)]
+CLASSES = [(3, 8), (3, 12), (3, 16), (3, 24), (3, 32), (6, 8), (6, 16)]
 
 
 def nvcc() -> str:

@@ -115,8 +115,8 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "this build supports p == 3, or p == 6 (two stacked passes)";
     return false;
   }
-  if (p->q != 8 && p->q != 16 && p->q != 32) {
-    why = "q must be 8, 16 or 32";
+  if (p->q != 8 && p->q != 12 && p->q != 16 && p->q != 24 && p->q != 32) {
+    why = "q must be 8, 12, 16, 24 or 32";
     return false;
   }
   if (p->r_a < 1 || p->r_a > 2) {
@@ -133,7 +133,11 @@ bool valid_params(const kstap_params* p, std::string& why) {
     return false;
   }
   if (p->r_b < 1 || p->r_b > kstap::kRbMax || p->r_b >= p->q) {
-    why = "r_b must satisfy 1 <= r_b <= 4 and r_b < q";
+    why = "r_b must satisfy 1 <= r_b <= 8 and r_b < q";
+    return false;
+  }
+  if (p->r_b > kstap::kRbFast && (p->p != 3 || p->precision != KSTAP_FP32)) {
+    why = "r_b > 4 runs with p == 3 on the KSTAP_FP32 bank";
     return false;
   }
   if (p->ring_r < 0 || p->ring_a < 0 || p->guard_r < 0 || p->guard_a < 0 ||
@@ -172,6 +176,14 @@ bool valid_params(const kstap_params* p, std::string& why) {
 }
 
 // Class-wide geometry (per-frame sizes are filled per tile from the job).
+// Cells per B-pass tile when the tuning leaves it open: the tile's B
+// matrices (q (q + 1) / 2 float-float entries per cell) and, for r_b > 4, the
+// block Rayleigh-Ritz scratch of four warps share the CTA's shared memory.
+int default_tc(const kstap_params& p) {
+  if (p.r_b > kstap::kRbFast) return p.q >= 24 ? 8 : 16;
+  return p.q >= 24 ? 16 : kstap::kTileCells;
+}
+
 Geom make_geom(const kstap_params& p, int V, int tc) {
   Geom g;
   g.p = p.p;
@@ -193,7 +205,7 @@ Geom make_geom(const kstap_params& p, int V, int tc) {
   g.max_iter = p.max_iter > 0 ? p.max_iter : 64;
   g.eps = p.eps > 0 ? (float)p.eps : 2e-6f;
   g.tau = p.tau;
-  g.tc = tc > 0 ? tc : ((p.q >= 32) ? 16 : kstap::kTileCells);
+  g.tc = tc > 0 ? tc : default_tc(p);
   g.filter = p.filter;
   return g;
 }
@@ -564,12 +576,12 @@ kstap_status kstap_create(const kstap_params* params, const kstap_c64* bank_a,
     for (const kstap_c64& z : hb) bmax = std::max(bmax, std::max(std::fabs(z.re), std::fabs(z.im)));
     const float sc = (bmax > 0.f && std::isfinite(bmax)) ? std::ldexp(1.f, -(std::ilogb(bmax) + 1)) : 1.f;
     ctx->bank_inv = 1.f / sc;
-    const int K2 = 2 * q;
+    const int K2 = kstap::tc_k2(q);   // 2 q columns (Re, Im), zero-padded to a multiple of 16
     const size_t half = (size_t)kstap::kTcM * K2 * 2;   // bytes of one 16-bit image
     std::vector<uint16_t> img(2 * half / 2, 0);
     const bool bf = params->precision == KSTAP_BF16X3;
     for (int v = 0; v < V; ++v)
-      for (int k = 0; k < K2; ++k) {
+      for (int k = 0; k < 2 * q; ++k) {
         const kstap_c64 z = hb[(size_t)v * q + (k % q)];
         const float x = (k < q ? z.re : z.im) * sc;
         uint16_t h, l;
@@ -824,8 +836,9 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   const Tuning saved = ctx->tune;
   const bool prof = ctx->profile;
   ctx->profile = false;
-  const std::vector<int> tcs =
-      (ctx->prm.q >= 32) ? std::vector<int>{8, 16} : std::vector<int>{16, 32};
+  const std::vector<int> tcs = (ctx->prm.q >= 24 || ctx->prm.r_b > kstap::kRbFast)
+                                    ? std::vector<int>{8, 16}
+                                    : std::vector<int>{16, 32};
   const int wavesv[] = {1, 2, 4, 8, 16};
   std::vector<int> stores{1};
   if (ctx->prm.p <= 3) stores.push_back(0);
@@ -839,7 +852,7 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   for (int tc : tcs) {
     const int ls = stores[li];
     std::string why;
-    if (!ls && !smem_fits(make_geom(ctx->prm, ctx->V, tc), false, why)) continue;
+    if (!smem_fits(make_geom(ctx->prm, ctx->V, tc), ls != 0, why)) continue;
     for (int w : wavesv) {
       ctx->tune.tc = tc;
       ctx->tune.waves = w;
@@ -870,7 +883,7 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   ctx->tune = bt;
   if (out) {
     out->waves = bt.waves;
-    out->tc = bt.tc > 0 ? bt.tc : ((ctx->prm.q >= 32) ? 16 : kstap::kTileCells);
+    out->tc = bt.tc > 0 ? bt.tc : default_tc(ctx->prm);
     out->lag_store = bt.lag_store;
     out->ms_per_batch = best;
   }
@@ -882,15 +895,13 @@ kstap_status kstap_set_tuning(kstap_ctx* ctx, const kstap_tuning* t) {
   if (t->waves < 1 || t->waves > 64) return fail(ctx, KSTAP_EINVAL, "waves must be in [1, 64]");
   if (t->tc != 0 && t->tc != 8 && t->tc != 16 && t->tc != 32)
     return fail(ctx, KSTAP_EINVAL, "tc must be 0, 8, 16 or 32");
-  if (t->tc == 32 && ctx->prm.q >= 32)
-    return fail(ctx, KSTAP_EINVAL, "tc = 32 does not fit shared memory at q = 32");
   if (t->lag_store != 0 && t->lag_store != 1)
     return fail(ctx, KSTAP_EINVAL, "lag_store must be 0 or 1");
   if (!t->lag_store && ctx->prm.p > 3)
     return fail(ctx, KSTAP_EINVAL, "stacked passes (p > 3) need the lag store");
   std::string why;
-  if (!t->lag_store && !smem_fits(make_geom(ctx->prm, ctx->V, t->tc), false, why))
-    return fail(ctx, KSTAP_EINVAL, "%s", why.c_str());
+  if (!smem_fits(make_geom(ctx->prm, ctx->V, t->tc), t->lag_store != 0, why))
+    return fail(ctx, KSTAP_EINVAL, "tc = %d: %s", t->tc, why.c_str());
   ctx->tune.waves = t->waves;
   ctx->tune.tc = t->tc;
   ctx->tune.lag_store = t->lag_store;

@@ -123,7 +123,9 @@ inline int tiles_mgram(int H, int W, int p) {
   return p <= 3 ? 0 : ((W + kstap::kStrip - 1) / kstap::kStrip) * H;   // a CTA per strip
 }
 inline int tiles_bfit(int H, int W, int tc) { return ((W + tc - 1) / tc) * H; }
-inline int cells_per_detect_block(int q) { return (kstap::kThreads / 32) * (32 / q); }
+inline int cells_per_detect_block(int q) {
+  return (kstap::kThreads / 32) * (32 / kstap::grp_lanes(q));
+}
 inline int tiles_detect(int H, int W, int q, int precision = KSTAP_FP32) {
   const int c = precision == KSTAP_FP32 ? cells_per_detect_block(q) : kstap::kTcCells;
   return (int)(((size_t)H * W + c - 1) / c);
@@ -192,7 +194,7 @@ kstap_status enqueue_scan(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const 
 
 // Per-class entry points: fit (scale, moments, flip-flop, B / U_B) and
 // detect (projection and bank) of every job of JL, for the r_b of g.
-#define KSTAP_CLASSES(X) X(3, 8) X(3, 16) X(3, 32) X(6, 8) X(6, 16)
+#define KSTAP_CLASSES(X) X(3, 8) X(3, 12) X(3, 16) X(3, 24) X(3, 32) X(6, 8) X(6, 16)
 #define KSTAP_DECLARE_CLASS(P, Q)                                                              \
   kstap_status fit_##P##_##Q(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL, \
                              char* scratch, const Layout& L, bool lag_store, int sm_count,     \

@@ -38,7 +38,13 @@ namespace kstap {
 
 constexpr int kTileCells = 32;      // cells of one range row per CTA (moments / B passes)
 constexpr int kThreads = 256;
-constexpr int kRbMax = 4;
+constexpr int kRbMax = 8;    // largest r_b
+constexpr int kRbFast = 4;   // r_b above this: every cell takes the block Rayleigh-Ritz path
+
+// Lanes of the group that holds one cell wherever a cell's q rows map onto
+// lanes (q <= 32): the next power of two, so that groups tile a warp; lanes
+// j >= q of a group hold no row and contribute zeros to the group sums.
+__host__ __device__ constexpr int grp_lanes(int q) { return q <= 8 ? 8 : q <= 16 ? 16 : 32; }
 constexpr float kBlindRefine = 1e-3f;   // |F_B b|^2 / |b|^2 below which w_b is refined in float-float
 constexpr int kBlindQ = 32;             // near-blind (cell, velocity) pairs queued per warp and pass
 constexpr float kLagNorm = 8.673617379884035e-19f;   // 2^-60: integer lag sums -> O(1) floats
@@ -1044,7 +1050,7 @@ __device__ __forceinline__ void b_times_v_fp32(const float4* __restrict__ Bc, in
   for (int m = 0; m < R; ++m) y[m] = make_float2(0.f, 0.f);
 #pragma unroll 4
   for (int t = 0; t < Q; ++t) {
-    const int l = (j + t) & (Q - 1);
+    const int l = (j + t < Q) ? j + t : j + t - Q;
     const float4 b = b_at<Q>(Bc, j, l);
     const float2 bh = make_float2(b.x, b.y);
 #pragma unroll
@@ -1074,17 +1080,18 @@ __device__ __forceinline__ ff grp_sum_ff(ff v) {
   return v;
 }
 
-// Modified Gram-Schmidt over the Q lanes of a group (FP32).
+// Modified Gram-Schmidt over the lanes of a group (FP32).
 template <int Q, int R>
 __device__ __forceinline__ void orthonormalise_g(float2 (&x)[R]) {
+  constexpr int G = grp_lanes(Q);
 #pragma unroll
   for (int m = 0; m < R; ++m) {
 #pragma unroll
     for (int mp = 0; mp < m; ++mp) {
-      const float2 cc = grp_sum2<Q>(cmulc(x[mp], x[m]));
+      const float2 cc = grp_sum2<G>(cmulc(x[mp], x[m]));
       x[m] = csub(x[m], cmul(x[mp], cc));
     }
-    const float nrm = sqrtf(grp_sum<Q>(cabs2(x[m])));
+    const float nrm = sqrtf(grp_sum<G>(cabs2(x[m])));
     x[m] = cscale(x[m], nrm > 0.f ? 1.f / nrm : 0.f);
   }
 }
@@ -1168,27 +1175,38 @@ constexpr int kSubSteps = 4;       // float-float subspace steps before a cell i
 // cells share a warp; `live` = this group's cell exists (dead groups compute
 // on zeros).
 template <int Q, int R>
-__device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live,
+__device__ bool eig_top_subspace(const float4* __restrict__ Bc, int jl, bool live,
                                  float2* __restrict__ Vs, float2 (&uh)[R], float2 (&ul)[R],
                                  float (&lam)[R]) {
+  constexpr int G = grp_lanes(Q);
+  // lane jl of the group holds row j = jl; lanes jl >= Q (q not a power of
+  // two) hold zeros and compute on row 0 without keeping the result
+  const bool row = jl < Q;
+  const int j = row ? jl : 0;
   float2 v[R], y[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const float4 b = b_at<Q>(Bc, j, ((2 * m + 1) * Q) / (2 * R));
-    v[m] = make_float2(b.x, b.y);
+    v[m] = row ? make_float2(b.x, b.y) : make_float2(0.f, 0.f);
   }
   orthonormalise_g<Q, R>(v);
+  if (row) {
 #pragma unroll
-  for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
+    for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
+  }
   __syncwarp();
   b_times_v_fp32<Q, R>(Bc, j, Vs, y);
+  if (!row) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) y[m] = make_float2(0.f, 0.f);
+  }
   __syncwarp();
   // Gram-Schmidt keeps orthonormality to ~eps cond(B V), which the change
   // measure of the float-float step below relies on (a one-pass Cholesky-QR
   // of the unnormalised start would leave ~eps cond^2)
   orthonormalise_g<Q, R>(y);
   // tr B (for the bound on lambda_{R+1})
-  const float trB = grp_sum<Q>(b_at<Q>(Bc, j, j).x);
+  const float trB = grp_sum<G>(row ? b_at<Q>(Bc, j, j).x : 0.f);
 #pragma unroll
   for (int m = 0; m < R; ++m) v[m] = y[m];
 
@@ -1196,8 +1214,10 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
   float2 H[R][R];
   bool converged = !live;
   for (int step = 0; step < kSubSteps; ++step) {
+    if (row) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
+      for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
+    }
     __syncwarp();
     // packed pairs: (re, im) += (br, bi) xr and (x, y) += (br, bi) (xi, -xi),
     // then re = re1 + y, im = im1 + x (error-free merge)
@@ -1206,7 +1226,7 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
     for (int m = 0; m < R; ++m) s1[m] = c1[m] = s2[m] = c2[m] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int t = 0; t < Q; ++t) {
-      const int l = (j + t) & (Q - 1);
+      const int l = (j + t < Q) ? j + t : j + t - Q;
       const float4 b = b_at<Q>(Bc, j, l);
       const float2 xh = make_float2(b.x, b.y), xl = make_float2(b.z, b.w);
       const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
@@ -1224,22 +1244,23 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
       float sr, er, si, ei;
       two_sum(s1[m].x, s2[m].y, sr, er);
       two_sum(s1[m].y, s2[m].x, si, ei);
-      Yf[m] = cff{ff_make(sr, __fadd_rn(er, __fadd_rn(c1[m].x, c2[m].y))),
-                  ff_make(si, __fadd_rn(ei, __fadd_rn(c1[m].y, c2[m].x)))};
+      Yf[m] = row ? cff{ff_make(sr, __fadd_rn(er, __fadd_rn(c1[m].x, c2[m].y))),
+                        ff_make(si, __fadd_rn(ei, __fadd_rn(c1[m].y, c2[m].x)))}
+                  : cff_zero();
     }
     // H = V^H Y (FP32), Gram G = Y^H Y (float-float)
 #pragma unroll
     for (int m = 0; m < R; ++m)
 #pragma unroll
       for (int mp = 0; mp < R; ++mp)
-        H[m][mp] = grp_sum2<Q>(cmulc(v[m], make_float2(Yf[mp].re.hi, Yf[mp].im.hi)));
+        H[m][mp] = grp_sum2<G>(cmulc(v[m], make_float2(Yf[mp].re.hi, Yf[mp].im.hi)));
     cff Gm[R][R];
 #pragma unroll
     for (int m = 0; m < R; ++m)
 #pragma unroll
       for (int mp = m; mp < R; ++mp) {
         const cff pr = cff_cmul(Yf[m], Yf[mp]);
-        Gm[m][mp] = cff{grp_sum_ff<Q>(pr.re), grp_sum_ff<Q>(pr.im)};
+        Gm[m][mp] = cff{grp_sum_ff<G>(pr.re), grp_sum_ff<G>(pr.im)};
       }
     // Cholesky G = L L^H
     cff L[R][R];
@@ -1285,7 +1306,7 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
         local += cabs2(X[m]);
       }
     }
-    const float change = grp_sum<Q>(local);
+    const float change = grp_sum<G>(local);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
     ritz_values<R>(H, lam);
@@ -1309,21 +1330,23 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int j, bool live
 // ------------------------------------------------ ill-gapped B -------------
 // EIG_{r_b} (Sec. 4) of a cell whose eigenvalue lambda_{R+1} lies close to
 // lambda_R, where subspace iteration on R vectors crawls: block subspace
-// iteration with K = min(Q, 8) vectors in float-float (kRrSteps steps; the
+// iteration with K = min(Q, max(8, R + 4)) vectors in float-float (kRrSteps steps; the
 // error of the leading R directions contracts by lambda_{K+1} / lambda_R per
 // step, and for Q <= 8 the block is the whole space), then Rayleigh-Ritz: the
 // K x K matrix V^H B V, diagonalised by a single-precision Jacobi (warm
 // start) and FP64 Jacobi sweeps on the rotated matrix, so that nearly equal
 // Ritz values are separated at double precision.  One warp per cell, lane j
 // < Q = row j.
-constexpr int kRrMaxK = 8;
+constexpr int kRrMinK = 8;
 constexpr int kRrSteps = 4;
-__host__ __device__ constexpr int rr_k(int q) { return q < kRrMaxK ? q : kRrMaxK; }
+__host__ __device__ constexpr int rr_k(int q, int r) {
+  return q < (r + 4 > kRrMinK ? r + 4 : kRrMinK) ? q : (r + 4 > kRrMinK ? r + 4 : kRrMinK);
+}
 // shared memory of one warp: the bases V and Y = B V [K][Q] float-float
 // complex (16 B), and four K x K matrices (FP64 H and Z1, FP32 H and Z0, 16 B
 // slots)
-__host__ __device__ constexpr int rr_bytes(int q) {
-  return 2 * rr_k(q) * q * 16 + 4 * rr_k(q) * rr_k(q) * 16;
+__host__ __device__ constexpr int rr_bytes(int q, int r) {
+  return 2 * rr_k(q, r) * q * 16 + 4 * rr_k(q, r) * rr_k(q, r) * 16;
 }
 
 template <typename T>
@@ -1461,7 +1484,7 @@ template <int Q, int R>
 __device__ __noinline__ void eig_block_rr(const float4* __restrict__ Bc,
                                           unsigned char* __restrict__ scr, int lane,
                                           float2 (&uh)[R], float2 (&ul)[R], float (&lam)[R]) {
-  constexpr int K = rr_k(Q);
+  constexpr int K = rr_k(Q, R);
   cff* Vs = reinterpret_cast<cff*>(scr);                                   // [K][Q]
   cff* Ys = Vs + K * Q;                                                    // [K][Q]
   cpx<double>* Hd = reinterpret_cast<cpx<double>*>(Ys + K * Q);            // [K][K]
@@ -1647,6 +1670,11 @@ __device__ __noinline__ void eig_block_rr(const float4* __restrict__ Bc,
 // most of shared memory and one CTA per SM must bring its own 16 warps.
 __host__ __device__ constexpr int bfit_threads(int q) { return q >= 32 ? 512 : kThreads; }
 
+// Warps of a B-pass CTA that run the block Rayleigh-Ritz path at once, each
+// with rr_bytes of scratch: one (for the few ill-gapped cells) when r_b <=
+// kRbFast, four when every cell takes that path (r_b > kRbFast).
+__host__ __device__ constexpr int bfit_rr_warps(int r) { return r > kRbFast ? 4 : 1; }
+
 constexpr int kLagStages = 4;   // lag-store prefetch depth of the B pass
 
 
@@ -1661,7 +1689,7 @@ __host__ __device__ constexpr int bfit_lag_bytes(int P, int Q, int TC, int Ra, b
          (from_store ? 0 : 2 * P * P * (TC + 2 * Ra + Q - 1) * 16);
 }
 __host__ __device__ constexpr int bfit_basis_bytes(int Q, int R) {
-  return (bfit_threads(Q) / 32) * (32 / Q) * Q * R * 8;
+  return R > kRbFast ? 0 : (bfit_threads(Q) / 32) * (32 / grp_lanes(Q)) * Q * R * 8;
 }
 __host__ __device__ constexpr int imax3(int a, int b, int c) {
   return a > b ? (a > c ? a : c) : (b > c ? b : c);
@@ -1671,7 +1699,8 @@ __host__ __device__ constexpr int imax3(int a, int b, int c) {
 // eigen phase and counts toward the fallback scratch.
 __host__ __device__ constexpr int bfit_region_bytes(int P, int Q, int R, int TC, int Ra, int Rr,
                                                      bool from_store) {
-  return imax3(bfit_lag_bytes(P, Q, TC, Ra, from_store), bfit_basis_bytes(Q, R), rr_bytes(Q)) +
+  return imax3(bfit_lag_bytes(P, Q, TC, Ra, from_store), bfit_basis_bytes(Q, R),
+               bfit_rr_warps(R) * rr_bytes(Q, R)) +
          (from_store ? 0 : P * (2 * Rr + 1) * (TC + 2 * Ra + Q - 1) * 8);
 }
 
@@ -1728,7 +1757,8 @@ __global__ void __launch_bounds__(bfit_threads(Q), 65536 / 128 / bfit_threads(Q)
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
-  constexpr int CPW = 32 / Q;   // cells per warp in the eigen phase
+  constexpr int GL = grp_lanes(Q);   // lanes per cell in the eigen phase
+  constexpr int CPW = 32 / GL;       // cells per warp in the eigen phase
   constexpr int NT = bfit_threads(Q);
   extern __shared__ __align__(16) unsigned char smem[];
   for (int tile = blockIdx.x; tile < JL.ntiles[kKindBfit]; tile += gridDim.x) {
@@ -1853,11 +1883,11 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
     }
   }
 
-  // eigen phase: a group of Q lanes per cell; cells whose subspace iteration
-  // does not converge (ill-gapped B) are queued for the block Rayleigh-Ritz
-  // phase below
+  // eigen phase: a group of GL lanes per cell; cells whose subspace
+  // iteration does not converge (ill-gapped B) are queued for the block
+  // Rayleigh-Ritz phase below, which takes every cell when r_b > kRbFast
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / Q, j = lane % Q;
+  const int sub = lane / GL, j = lane % GL;
   const int slot = warp * CPW + sub;
   const int per_pass = (NT / 32) * CPW;
   // writes U_B (row j of cell cl) and, from lane j == 0, lambda_B
@@ -1884,34 +1914,44 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   __shared__ int fb_cell[kTileCells];
   if (threadIdx.x == 0) fb_n = 0;
   __syncthreads();
-  for (int base = 0; base < TC; base += per_pass) {
-    const int cl = base + slot;
-    const bool live = cl < TC && (c0 + cl) < g.W;
-    const int clc = live ? cl : 0;
-    float2 uh[R], ul[R];
-    float lam[R];
-    const bool conv = eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
-    if (live && conv) store(cl, j, uh, ul, lam);
-    if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
+  if constexpr (R > kRbFast) {
+    for (int cl = threadIdx.x; cl < TC; cl += NT)
+      if (c0 + cl < g.W) fb_cell[atomicAdd(&fb_n, 1)] = cl;
+  } else {
+    for (int base = 0; base < TC; base += per_pass) {
+      const int cl = base + slot;
+      const bool live = cl < TC && (c0 + cl) < g.W;
+      const int clc = live ? cl : 0;
+      float2 uh[R], ul[R];
+      float lam[R];
+      const bool conv =
+          eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
+      if (live && conv && j < Q) store(cl, j, uh, ul, lam);
+      if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
+    }
   }
   __syncthreads();
   const int nfb = fb_n;
   if (nfb > 0) {
-    // one warp per queued cell, each with rr_bytes(Q) of the (now dead) lag
-    // and basis scratch
-    const int slots = min(NT / 32, bfit_region_bytes(P, Q, R, TC, g.Ra, g.Rr, FROM_STORE) / rr_bytes(Q));
+    // one warp per queued cell, each with rr_bytes of the (now dead) lag and
+    // basis scratch
+    constexpr int RB = rr_bytes(Q, R);
+    const int slots = min(NT / 32, bfit_region_bytes(P, Q, R, TC, g.Ra, g.Rr, FROM_STORE) / RB);
     if (warp < slots) {
       for (int e = warp; e < nfb; e += slots) {
         const int cl = fb_cell[e];
         float2 uh[R], ul[R];
         float lam[R];
-        eig_block_rr<Q, R>(Bs + cl * NB, reinterpret_cast<unsigned char*>(lag) + warp * rr_bytes(Q),
-                           lane, uh, ul, lam);
+        eig_block_rr<Q, R>(Bs + cl * NB, reinterpret_cast<unsigned char*>(lag) + warp * RB, lane,
+                           uh, ul, lam);
         if (lane < Q) store(cl, lane, uh, ul, lam);
         __syncwarp();
       }
     }
-    if (threadIdx.x == 0 && JL.report) atomicAdd(JL.report + 2, (unsigned long long)nfb);
+    // the ill-gapped count (with r_b > kRbFast every cell takes this path
+    // and none is counted)
+    if (R <= kRbFast && threadIdx.x == 0 && JL.report)
+      atomicAdd(JL.report + 2, (unsigned long long)nfb);
   }
   __syncthreads();
   }  // tile loop
@@ -1933,10 +1973,10 @@ template <int P, int Q, int R, int RA = 1>
 __global__ void __launch_bounds__(kThreads)
 k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
          const float2* __restrict__ bank_bT, const float* __restrict__ bank_n2) {
-  constexpr int G = Q;                         // lanes per cell
+  constexpr int G = grp_lanes(Q);              // lanes per cell (lanes >= Q hold no column)
   constexpr int CPW = 32 / G;                  // cells per warp
   constexpr int CPB = (kThreads / 32) * CPW;   // cells per block
-  constexpr int VB = 4;                        // velocities per lane per pass
+  constexpr int VB = R > kRbFast ? 2 : 4;      // velocities per lane per pass
   // float2 scratch per cell (even, so every cell's float4 blocks stay
   // 16-byte aligned)
   constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 4 * P * R;
@@ -1975,14 +2015,16 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
       const size_t cn = (size_t)ltn * CPB + slot;
       if (cn < (size_t)JN.H * JN.W) {
         const int r = (int)(cn / JN.W), c = (int)(cn % JN.W);
+        if (gl < Q) {
 #pragma unroll
-        for (int i = 0; i < P; ++i)
-          cp_async8(pf + i * Q + gl, JN.Y + (size_t)i * JN.ch_stride +
-                                         (size_t)(r + g0.Rr) * JN.W_in + (c + g0.Ra + gl));
+          for (int i = 0; i < P; ++i)
+            cp_async8(pf + i * Q + gl, JN.Y + (size_t)i * JN.ch_stride +
+                                           (size_t)(r + g0.Rr) * JN.W_in + (c + g0.Ra + gl));
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-          cp_async8(pf + P * Q + gl * R + m, JN.UBh + (cn * Q + gl) * R + m);
-          cp_async8(pf + P * Q + Q * R + gl * R + m, JN.UBl + (cn * Q + gl) * R + m);
+          for (int m = 0; m < R; ++m) {
+            cp_async8(pf + P * Q + gl * R + m, JN.UBh + (cn * Q + gl) * R + m);
+            cp_async8(pf + P * Q + Q * R + gl * R + m, JN.UBl + (cn * Q + gl) * R + m);
+          }
         }
         for (int e = gl; e < P * RA; e += G)
           cp_async8(pf + P * Q + 2 * Q * R + e, JN.UA + cn * P * RA + e);
@@ -2010,12 +2052,14 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   float4* Es = Cs + P * R;                               // [P][R] F_A C, float-float (classical)
   cp_async_wait<0>();
   if (live) {
+    if (gl < Q) {
 #pragma unroll
-    for (int i = 0; i < P; ++i) Xs[i * Q + gl] = pf[i * Q + gl];
+      for (int i = 0; i < P; ++i) Xs[i * Q + gl] = pf[i * Q + gl];
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      Uh[gl * R + m] = pf[P * Q + gl * R + m];
-      Ul[gl * R + m] = pf[P * Q + Q * R + gl * R + m];
+      for (int m = 0; m < R; ++m) {
+        Uh[gl * R + m] = pf[P * Q + gl * R + m];
+        Ul[gl * R + m] = pf[P * Q + Q * R + gl * R + m];
+      }
     }
     for (int e = gl; e < P * RA; e += G) Ua[e] = pf[P * Q + 2 * Q * R + e];   // [i][m]
   }
@@ -2083,7 +2127,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   }
   // Z1 = X - C U^T (float-float) then Z = F_A Z1 (Kron) or Z = Z1 (classical);
   // lane gl owns column j = gl
-  if (live) {
+  if (live && gl < Q) {
     const int j = gl;
     float2 uh[R], ul[R];
 #pragma unroll
@@ -2268,7 +2312,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
 #pragma unroll
         for (int i = 0; i < P; ++i) yv[i] = make_float2(0.f, 0.f);
         float dBn = 0.f;
-        if (act) {
+        if (act && gl < Q) {
           const int v = qi[it] & 0xffff, cs = qi[it] >> 16;
           const float2* sc = scr + (warp * CPW + cs) * CS;
           const float2* Zc = sc + P * Q;

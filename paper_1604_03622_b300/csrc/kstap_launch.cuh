@@ -109,7 +109,7 @@ kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, cons
                             int sm_count, int waves, cudaStream_t s) {
   if (JL.njobs < 1) return KSTAP_OK;
   if (g.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
-  if constexpr (P <= 3) {
+  if constexpr (P <= 3 && R <= kstap::kRbFast) {
     if (ctx->prm.precision == KSTAP_FP16X3)
       return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
     if (ctx->prm.precision == KSTAP_BF16X3)
@@ -136,29 +136,38 @@ kstap_status enqueue_detect_fp32(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g,
 }
 
 // r_b dispatch of one class: defines fit_P_Q / detect_P_Q (declared in
-// kstap_host.cuh) for r_b in [1, 4], r_b < q.
+// kstap_host.cuh) for r_b in [1, 8] (p <= 3) or [1, 4] (stacked passes),
+// r_b < q.
+template <int P, int Q, int R = 1>
+kstap_status fit_rb(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                    char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
+                    cudaStream_t s) {
+  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : kstap::kRbFast)) {
+    if (g.r_b == R)
+      return enqueue_fit<P, Q, R>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);
+    return fit_rb<P, Q, R + 1>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);
+  }
+  return fail(ctx, KSTAP_EINVAL, "unsupported r_b %d", g.r_b);
+}
+template <int P, int Q, int R = 1>
+kstap_status detect_rb(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
+                       int sm_count, int waves, cudaStream_t s) {
+  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : kstap::kRbFast)) {
+    if (g.r_b == R) return enqueue_detect<P, Q, R>(ctx, prof, g, JL, sm_count, waves, s);
+    return detect_rb<P, Q, R + 1>(ctx, prof, g, JL, sm_count, waves, s);
+  }
+  return fail(ctx, KSTAP_EINVAL, "unsupported r_b %d", g.r_b);
+}
 #define KSTAP_DEFINE_FIT_(P, Q)                                                                \
   kstap_status fit_##P##_##Q(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL, \
                              char* scratch, const Layout& L, bool lag_store, int sm_count,     \
                              int waves, cudaStream_t s) {                                       \
-    switch (g.r_b) {                                                                            \
-      case 1: return enqueue_fit<P, Q, 1>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s); \
-      case 2: return enqueue_fit<P, Q, 2>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s); \
-      case 3: return enqueue_fit<P, Q, 3>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s); \
-      case 4: return enqueue_fit<P, Q, 4>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s); \
-    }                                                                                           \
-    return fail(ctx, KSTAP_EINVAL, "unsupported r_b %d", g.r_b);                                \
+    return fit_rb<P, Q>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);          \
   }
 #define KSTAP_DEFINE_DETECT_(P, Q)                                                             \
   kstap_status detect_##P##_##Q(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g,               \
                                 const JobList& JL, int sm_count, int waves, cudaStream_t s) {  \
-    switch (g.r_b) {                                                                            \
-      case 1: return enqueue_detect<P, Q, 1>(ctx, prof, g, JL, sm_count, waves, s);             \
-      case 2: return enqueue_detect<P, Q, 2>(ctx, prof, g, JL, sm_count, waves, s);             \
-      case 3: return enqueue_detect<P, Q, 3>(ctx, prof, g, JL, sm_count, waves, s);             \
-      case 4: return enqueue_detect<P, Q, 4>(ctx, prof, g, JL, sm_count, waves, s);             \
-    }                                                                                           \
-    return fail(ctx, KSTAP_EINVAL, "unsupported r_b %d", g.r_b);                                \
+    return detect_rb<P, Q>(ctx, prof, g, JL, sm_count, waves, s);                              \
   }
 #define KSTAP_DEFINE_FIT(P, Q) KSTAP_DEFINE_FIT_(P, Q)
 #define KSTAP_DEFINE_DETECT(P, Q) KSTAP_DEFINE_DETECT_(P, Q)

@@ -36,6 +36,10 @@ constexpr long long kTcWaitCycles = 1ll << 30;   // ~0.5 s at 2 GHz: bound of on
 
 __host__ __device__ constexpr int tc_threads(int q) { return q >= 32 ? 512 : 256; }
 
+// Contraction length of the bank GEMM: (Re, Im) x q real columns, padded
+// with zero columns to whole MMA K steps of 16 (q = 12: 24 -> 32).
+__host__ __device__ constexpr int tc_k2(int q) { return ((2 * q + 15) / 16) * 16; }
+
 // K-major, no-swizzle core-matrix layout of a 16-bit operand with `rows`
 // rows: a core matrix is 8 rows x 16 bytes (8 elements) stored contiguously.
 // K advances in blocks of 16 elements (one MMA step); inside a block, row
@@ -130,8 +134,8 @@ __host__ __device__ constexpr int tc_scratch(int P, int Q, int R) {
 
 // Dynamic shared memory of k_detect_tc (host and device agree on it).
 __host__ __device__ constexpr size_t tc_smem_bytes(int P, int Q, int R) {
-  return 2 * (size_t)kTcM * 2 * Q * 2          // bank operand, hi and lo
-         + 2 * (size_t)kTcN * 2 * Q * 2        // cell operand, hi and lo
+  return 2 * (size_t)kTcM * tc_k2(Q) * 2       // bank operand, hi and lo
+         + 2 * (size_t)kTcN * tc_k2(Q) * 2     // cell operand, hi and lo
          + (size_t)kTcCells * tc_scratch(P, Q, R) * 8
          + (size_t)kTcCells * kTcM * 4         // T of the tile, for the argmax
          + (size_t)kTcCells * kTcM * 4;        // queue of (cell, v) to recompute
@@ -155,8 +159,8 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
             const float2* __restrict__ bank_aT, const float2* __restrict__ bank_bT,
             const float* __restrict__ bank_n2, unsigned* __restrict__ fault) {
   constexpr int NT = tc_threads(Q);
-  constexpr int G = Q;                       // lanes per cell in the projection phase
-  constexpr int K2 = 2 * Q;                  // real contraction length
+  constexpr int G = grp_lanes(Q);            // lanes per cell in the projection phase
+  constexpr int K2 = tc_k2(Q);               // real contraction length (zero-padded)
   constexpr int ROWS = 2 * (P + R);          // operand rows used per cell
   static_assert(ROWS <= kTcRowsPerCell, "p + r_b > 8");
   constexpr int SCR = tc_scratch(P, Q, R);   // float2 per cell (even: float4 alignment)
@@ -236,14 +240,16 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
       float* scl = reinterpret_cast<float*>(Es + P * R);
       if (live) {
         const int r = (int)(cell / g.W), cc = (int)(cell % g.W);
+        if (gl < Q) {
 #pragma unroll
-        for (int i = 0; i < P; ++i)
-          Xs[i * Q + gl] =
-              __ldg(JB.Y + (size_t)i * g.ch_stride + (size_t)(r + g.Rr) * g.W_in + (cc + g.Ra + gl));
+          for (int i = 0; i < P; ++i)
+            Xs[i * Q + gl] = __ldg(JB.Y + (size_t)i * g.ch_stride + (size_t)(r + g.Rr) * g.W_in +
+                                   (cc + g.Ra + gl));
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-          Uh[gl * R + m] = JB.UBh[(cell * Q + gl) * R + m];
-          Ul[gl * R + m] = JB.UBl[(cell * Q + gl) * R + m];
+          for (int m = 0; m < R; ++m) {
+            Uh[gl * R + m] = JB.UBh[(cell * Q + gl) * R + m];
+            Ul[gl * R + m] = JB.UBl[(cell * Q + gl) * R + m];
+          }
         }
         if (gl < P) Ua[gl] = JB.UA[cell * P + gl];
       }
@@ -269,7 +275,7 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
       __syncwarp();
       float2 z[P];
       float zmax = 0.f;
-      if (live) {
+      if (live && gl < Q) {
         const int j = gl;
         float2 uh[R], ul[R];
 #pragma unroll
@@ -318,7 +324,7 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
       // precision independent of the frame's amplitude
       const float sc = (zmax > 0.f && zmax <= kFltMax) ? ldexpf(1.f, -(ilogbf(zmax) + 1)) : 1.f;
       if (live && gl == 0) *scl = sc;
-      if (live) {
+      if (live && gl < Q) {
         // complex row t: Z[t] * sc (t < P), U_hi[:, t - P] (t < P + R); real
         // rows n = 2t: (Re | Im), n = 2t + 1: (Im | -Re)
         const int j = gl;
@@ -446,8 +452,10 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
         const float2* Uh = Zs + P * Q;
         const float2* Ul = Uh + Q * R;
         const float2* Ua = Ul + Q * R;
-        const int j = gl;
-        const float2 b = __ldg(bank_bT + j * V + vq);
+        // lane gl = pulse j; lanes gl >= Q (no pulse) read row 0 and add zeros
+        const bool prow = gl < Q;
+        const int j = prow ? gl : 0;
+        const float2 b = prow ? __ldg(bank_bT + j * V + vq) : make_float2(0.f, 0.f);
         float2 Gm[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) Gm[m] = grp_sum2<G>(cmulc(Uh[j * R + m], b));
@@ -464,7 +472,8 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
           ci = __fmaf_rn(-ul.x, Gm[m].y, ci);
           ci = __fmaf_rn(-ul.y, Gm[m].x, ci);
         }
-        const float2 w = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+        const float2 w = prow ? make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci))
+                              : make_float2(0.f, 0.f);
         const float dB = grp_sum<G>(cabs2(w));
         float2 y[P];
 #pragma unroll

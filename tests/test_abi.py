@@ -33,12 +33,16 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_create_rejects_unsupported_parameters_without_gpu():
     bad = [
         K.make_params(4, 16, 1, 3, 4, 7, 1, 2, 10.0),    # p != 3
-        K.make_params(3, 12, 1, 3, 4, 7, 1, 2, 10.0),    # q not in {8,16,32}
+        K.make_params(3, 10, 1, 3, 4, 7, 1, 2, 10.0),    # q not in {8,12,16,24,32}
+        K.make_params(3, 48, 1, 3, 4, 7, 1, 2, 10.0),    # q > 32
         K.make_params(3, 16, 3, 3, 4, 7, 1, 2, 10.0),    # r_a > 2
         K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0, precision="fp16x3"),   # r_a = 2: FP32 bank
         K.make_params(3, 16, 2, 3, 4, 7, 1, 2, 10.0, filter="classical"),   # r_a = 2: Kron filter
         K.make_params(3, 8, 1, 8, 3, 4, 1, 2, 10.0),     # r_b >= q (Sec. 5)
-        K.make_params(3, 16, 1, 5, 4, 7, 1, 2, 10.0),    # r_b > 4
+        K.make_params(3, 16, 1, 9, 4, 7, 1, 2, 10.0),    # r_b > 8
+        K.make_params(3, 12, 1, 12, 4, 7, 1, 2, 10.0),   # r_b >= q
+        K.make_params(3, 16, 1, 5, 4, 7, 1, 2, 10.0, precision="fp16x3"),   # r_b > 4: FP32 bank
+        K.make_params(6, 16, 1, 5, 4, 7, 1, 2, 10.0),    # r_b > 4: p = 3
         K.make_params(3, 16, 1, 3, 1, 7, 2, 2, 10.0),    # guard > ring
         K.make_params(3, 16, 1, 3, 0, 0, 0, 0, 10.0),    # empty ring
         K.make_params(3, 16, 1, 3, 12, 24, 1, 1, 10.0),  # box > 1024
@@ -54,6 +58,19 @@ def test_create_rejects_unsupported_parameters_without_gpu():
         with pytest.raises(K.KstapError, match="EINVAL"):
             K.kstap_create(prm, _Fake(dummy), _Fake(dummy), 8)
         assert K.kstap_last_error(None) != ""
+
+
+def test_domain_accepted_by_validation_without_gpu():
+    """q in {8, 12, 16, 24, 32} and 1 <= r_b <= min(q - 1, 8) pass the checks
+    that run before any device work: the workspace size is defined for them."""
+    for q in (8, 12, 16, 24, 32):
+        for r_b in range(1, min(q - 1, 8) + 1):
+            prm = K.make_params(3, q, 1, r_b, 4, 7, 1, 2, 10.0)
+            assert K.kstap_workspace_bytes(prm, 40, 40 + q) > 0, (q, r_b)
+    for q in (12, 24):
+        for prec in ("fp16x3", "bf16x3"):
+            prm = K.make_params(3, q, 1, 4, 4, 7, 1, 2, 10.0, precision=prec)
+            assert K.kstap_workspace_bytes(prm, 40, 40 + q) > 0, (q, prec)
 
 
 def test_noalloc_and_change_map_reject_without_gpu():

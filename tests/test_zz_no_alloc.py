@@ -47,8 +47,9 @@ def _fit_and_detect(K, ks, Y, H_in, W_in, noalloc):
     return out
 
 
-# (workload, cell grid): q = 8, 16 and 32, each with ragged tiles
-CASES = [("small64", 48, 70), ("frame1024", 40, 90), ("precision2048", 24, 72)]
+# (workload, cell grid): q = 8, 12, 16, 24 and 32, each with ragged tiles
+CASES = [("small64", 48, 70), ("frame_q12", 30, 61), ("frame1024", 40, 90),
+         ("frame_q24", 20, 50), ("precision2048", 24, 72)]
 
 
 @pytest.mark.parametrize("name,H,W", CASES)
