@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg on the 256-tile workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-domain", action="store_true",
+                    help="skip the q = 12 / 24 and r_b > 4 frames")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests in the Poisson serving stream")
     ap.add_argument("--cells", type=int, nargs=2, metavar=("H", "W"),
@@ -499,6 +501,68 @@ def precision_leg(dev, steps: int, warmup: int, err_cells: int = 256, cpu: bool 
     return out
 
 
+# ------------------------------------------- the rest of the (q, r_b) domain ---
+def domain_leg(dev, steps: int, warmup: int, err_cells: int = 256, cpu: bool = True):
+    """Frames of 1024 x 1024 cells at the window lengths and ranks between and
+    above the configurations': q = 12 (r_b = 3, n = 72) and q = 24 (r_b = 4,
+    n = 144) on the FP32 and FP16X3 banks, and r_b = 8 at q = 16 and r_b = 6 at
+    q = 32 (block Rayleigh-Ritz path, FP32 bank); plain path, CUDA events per
+    frame with an L2 flush between frames, per-kernel times, and the error of
+    T against the FP64 oracle on `err_cells` seeded cells (all velocities)."""
+    import dataclasses
+    import torch
+    import gen
+    import paper_1604_03622_b300 as K
+    from paper_1604_03622_b300.runner import KStap
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    cases = [("frame_q12", 3, "fp32"), ("frame_q12", 3, "fp16x3"), ("frame_q24", 4, "fp32"),
+             ("frame_q24", 4, "fp16x3"), ("frame1024", 8, "fp32"), ("precision2048", 6, "fp32")]
+    rows = []
+    for name, r_b, prec in cases:
+        wl = dataclasses.replace(gen.WORKLOADS[name], r_b=r_b).with_size(1024, 1024)
+        f = gen.make_frame(wl)
+        Y = torch.from_numpy(f.Y).to(dev)
+        ks = KStap.from_workload(wl, f.bank_a, f.bank_b, device=str(dev), stream=stream,
+                                 precision=prec)
+        for _ in range(warmup):
+            ks.run(Y)
+        torch.cuda.synchronize(dev)
+        K.kstap_set_profiling(ks.ctx, True)
+        ms = []
+        for s_ in range(steps):
+            flush.fill_(s_ & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ks.run(Y)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        kt = K.kstap_kernel_times(ks.ctx)
+        K.kstap_set_profiling(ks.ctx, False)
+        err = None
+        if cpu and err_cells > 0:
+            import oracle
+            cells = gen.random_cells(wl, err_cells, seed=78)
+            ref = oracle.run_workload(f, cells=cells, want_proj=False)
+            T = ks.run(Y, T_all=True)["T_all"][torch.from_numpy(ref["cells"]).to(dev)]
+            T = T.double().cpu().numpy()
+            ok = ref["gapB"] >= 1e-6
+            e = np.abs(T - ref["T_all"]) / np.maximum(ref["T_all"], wl.sigma2)
+            err = dict(max_rel_err_T=float(e[ok].max()) if ok.any() else None,
+                       cells=int(len(cells)), cells_gap_below_1e_6=int((~ok).sum()))
+        ks.close()
+        rows.append(dict(workload=wl.name, q=wl.q, r_b=wl.r_b, n=wl.n, V=wl.V, precision=prec,
+                         cells_per_s=wl.cells * len(ms) / (sum(ms) / 1e3),
+                         ms_per_frame=sum(ms) / len(ms), error=err,
+                         kernel_ms_per_launch={k: v[0] / max(v[1], 1) for k, v in kt.items()}))
+        del Y
+    del flush
+    torch.cuda.empty_cache()
+    return dict(rows=rows, note="error: max |T - T_ref| / max(T_ref, sigma^2) over the sampled "
+                               "cells whose oracle eigengap of B is >= 1e-6")
+
+
 # --------------------------------------------------- robustness (Sec. 5) ---
 def robustness_leg(dev):
     """Detection on synthetic data under the SIRV texture and corrupted
@@ -886,6 +950,8 @@ def main():
 
     robustness = None if args.no_robustness else robustness_leg(dev)
 
+    domain = None if args.no_domain else domain_leg(dev, 3, 2, cpu=not args.no_cpu_baseline)
+
     multipass = None if args.no_multipass else multipass_leg(dev, 3, 2)
 
     paper_timing = None if args.no_paper_timing else paper_timing_leg(
@@ -940,7 +1006,7 @@ def main():
         roofline=roof, cpu_baseline=cpu, clocks=clocks, wall_s_timed_loop=t_wall,
         batched_vs_plain=bvp or None,
         batched=batched, serving=serving, precision_q32=precision, paper_timing=paper_timing,
-        robustness=robustness, multipass=multipass)
+        robustness=robustness, multipass=multipass, domain=domain)
     print(json.dumps(line), flush=True)
     ks.close()
     if ws > 1:

@@ -68,9 +68,9 @@ typedef enum {
  * channels stacked as one frame (Sec. 3), spatial rank r_a in {1, 2} -- with
  * q in {8, 16}, the KSTAP_FP32 bank and the Kron-STAP filter.
  * 1 <= r_b <= min(q - 1, 8) (Sec. 5 warns against r_b close to q); r_b > 4
- * needs p == 3 and the KSTAP_FP32 bank, and every cell's U_B then comes from
- * block subspace iteration with an FP64 Rayleigh-Ritz step (slower than the
- * r_b <= 4 path).  ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1)
+ * needs p == 3 and the KSTAP_FP32 bank (the B pass's r_b x r_b Gram and
+ * Cholesky factors then exceed the registers, and it runs 10-30 times slower
+ * than at r_b = 3).  ring >= guard >= 0, n >= 1, (2 ring_r + 1)(2 ring_a + 1)
  * <= 1024, and a training box whose tiles fit shared memory.  Other values
  * give KSTAP_EINVAL. */
 typedef struct {
@@ -153,8 +153,7 @@ kstap_status kstap_fit_project(kstap_ctx* ctx, const kstap_c64* Y, int H_in, int
  * rate estimate left more than ~2e-7 of subspace error after 4 steps), so
  * U_B and lambda_B were recomputed by block subspace iteration on
  * min(q, max(8, r_b + 4)) vectors with a Rayleigh-Ritz step solved by FP64
- * Jacobi sweeps.  With r_b > 4 every cell takes that path and eig_refined
- * stays 0.  Any pointer may be NULL.  Returns KSTAP_WARN_NOCONV if any cell stopped at
+ * Jacobi sweeps.  Any pointer may be NULL.  Returns KSTAP_WARN_NOCONV if any cell stopped at
  * max_iter (its factors are the last iterate, valid but not converged to
  * eps), else KSTAP_OK. */
 kstap_status kstap_fit_report(kstap_ctx* ctx, long long* nonconverged, long long* nonfinite,

@@ -136,7 +136,7 @@ bool valid_params(const kstap_params* p, std::string& why) {
     why = "r_b must satisfy 1 <= r_b <= 8 and r_b < q";
     return false;
   }
-  if (p->r_b > kstap::kRbFast && (p->p != 3 || p->precision != KSTAP_FP32)) {
+  if (p->r_b > kstap::kRbTc && (p->p != 3 || p->precision != KSTAP_FP32)) {
     why = "r_b > 4 runs with p == 3 on the KSTAP_FP32 bank";
     return false;
   }
@@ -177,12 +177,9 @@ bool valid_params(const kstap_params* p, std::string& why) {
 
 // Class-wide geometry (per-frame sizes are filled per tile from the job).
 // Cells per B-pass tile when the tuning leaves it open: the tile's B
-// matrices (q (q + 1) / 2 float-float entries per cell) and, for r_b > 4, the
-// block Rayleigh-Ritz scratch of four warps share the CTA's shared memory.
-int default_tc(const kstap_params& p) {
-  if (p.r_b > kstap::kRbFast) return p.q >= 24 ? 8 : 16;
-  return p.q >= 24 ? 16 : kstap::kTileCells;
-}
+// matrices (q (q + 1) / 2 float-float entries per cell) fill most of the
+// CTA's shared memory at q >= 24.
+int default_tc(const kstap_params& p) { return p.q >= 24 ? 16 : kstap::kTileCells; }
 
 Geom make_geom(const kstap_params& p, int V, int tc) {
   Geom g;
@@ -836,9 +833,8 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   const Tuning saved = ctx->tune;
   const bool prof = ctx->profile;
   ctx->profile = false;
-  const std::vector<int> tcs = (ctx->prm.q >= 24 || ctx->prm.r_b > kstap::kRbFast)
-                                    ? std::vector<int>{8, 16}
-                                    : std::vector<int>{16, 32};
+  const std::vector<int> tcs =
+      (ctx->prm.q >= 24) ? std::vector<int>{8, 16} : std::vector<int>{16, 32};
   const int wavesv[] = {1, 2, 4, 8, 16};
   std::vector<int> stores{1};
   if (ctx->prm.p <= 3) stores.push_back(0);

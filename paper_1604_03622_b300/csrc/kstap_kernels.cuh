@@ -39,7 +39,7 @@ namespace kstap {
 constexpr int kTileCells = 32;      // cells of one range row per CTA (moments / B passes)
 constexpr int kThreads = 256;
 constexpr int kRbMax = 8;    // largest r_b
-constexpr int kRbFast = 4;   // r_b above this: every cell takes the block Rayleigh-Ritz path
+constexpr int kRbTc = 4;     // largest r_b of the tensor-core bank (2 (p + r_b) <= 16 operand rows)
 
 // Lanes of the group that holds one cell wherever a cell's q rows map onto
 // lanes (q <= 32): the next power of two, so that groups tile a warp; lanes
@@ -1670,10 +1670,6 @@ __device__ __noinline__ void eig_block_rr(const float4* __restrict__ Bc,
 // most of shared memory and one CTA per SM must bring its own 16 warps.
 __host__ __device__ constexpr int bfit_threads(int q) { return q >= 32 ? 512 : kThreads; }
 
-// Warps of a B-pass CTA that run the block Rayleigh-Ritz path at once, each
-// with rr_bytes of scratch: one (for the few ill-gapped cells) when r_b <=
-// kRbFast, four when every cell takes that path (r_b > kRbFast).
-__host__ __device__ constexpr int bfit_rr_warps(int r) { return r > kRbFast ? 4 : 1; }
 
 constexpr int kLagStages = 4;   // lag-store prefetch depth of the B pass
 
@@ -1689,7 +1685,7 @@ __host__ __device__ constexpr int bfit_lag_bytes(int P, int Q, int TC, int Ra, b
          (from_store ? 0 : 2 * P * P * (TC + 2 * Ra + Q - 1) * 16);
 }
 __host__ __device__ constexpr int bfit_basis_bytes(int Q, int R) {
-  return R > kRbFast ? 0 : (bfit_threads(Q) / 32) * (32 / grp_lanes(Q)) * Q * R * 8;
+  return (bfit_threads(Q) / 32) * (32 / grp_lanes(Q)) * Q * R * 8;
 }
 __host__ __device__ constexpr int imax3(int a, int b, int c) {
   return a > b ? (a > c ? a : c) : (b > c ? b : c);
@@ -1699,8 +1695,7 @@ __host__ __device__ constexpr int imax3(int a, int b, int c) {
 // eigen phase and counts toward the fallback scratch.
 __host__ __device__ constexpr int bfit_region_bytes(int P, int Q, int R, int TC, int Ra, int Rr,
                                                      bool from_store) {
-  return imax3(bfit_lag_bytes(P, Q, TC, Ra, from_store), bfit_basis_bytes(Q, R),
-               bfit_rr_warps(R) * rr_bytes(Q, R)) +
+  return imax3(bfit_lag_bytes(P, Q, TC, Ra, from_store), bfit_basis_bytes(Q, R), rr_bytes(Q, R)) +
          (from_store ? 0 : P * (2 * Rr + 1) * (TC + 2 * Ra + Q - 1) * 8);
 }
 
@@ -1885,7 +1880,7 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
 
   // eigen phase: a group of GL lanes per cell; cells whose subspace
   // iteration does not converge (ill-gapped B) are queued for the block
-  // Rayleigh-Ritz phase below, which takes every cell when r_b > kRbFast
+  // Rayleigh-Ritz phase below
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / GL, j = lane % GL;
   const int slot = warp * CPW + sub;
@@ -1914,21 +1909,16 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   __shared__ int fb_cell[kTileCells];
   if (threadIdx.x == 0) fb_n = 0;
   __syncthreads();
-  if constexpr (R > kRbFast) {
-    for (int cl = threadIdx.x; cl < TC; cl += NT)
-      if (c0 + cl < g.W) fb_cell[atomicAdd(&fb_n, 1)] = cl;
-  } else {
-    for (int base = 0; base < TC; base += per_pass) {
-      const int cl = base + slot;
-      const bool live = cl < TC && (c0 + cl) < g.W;
-      const int clc = live ? cl : 0;
-      float2 uh[R], ul[R];
-      float lam[R];
-      const bool conv =
-          eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
-      if (live && conv && j < Q) store(cl, j, uh, ul, lam);
-      if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
-    }
+  for (int base = 0; base < TC; base += per_pass) {
+    const int cl = base + slot;
+    const bool live = cl < TC && (c0 + cl) < g.W;
+    const int clc = live ? cl : 0;
+    float2 uh[R], ul[R];
+    float lam[R];
+    const bool conv =
+        eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
+    if (live && conv && j < Q) store(cl, j, uh, ul, lam);
+    if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
   }
   __syncthreads();
   const int nfb = fb_n;
@@ -1948,10 +1938,7 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
         __syncwarp();
       }
     }
-    // the ill-gapped count (with r_b > kRbFast every cell takes this path
-    // and none is counted)
-    if (R <= kRbFast && threadIdx.x == 0 && JL.report)
-      atomicAdd(JL.report + 2, (unsigned long long)nfb);
+    if (threadIdx.x == 0 && JL.report) atomicAdd(JL.report + 2, (unsigned long long)nfb);
   }
   __syncthreads();
   }  // tile loop
@@ -1976,7 +1963,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   constexpr int G = grp_lanes(Q);              // lanes per cell (lanes >= Q hold no column)
   constexpr int CPW = 32 / G;                  // cells per warp
   constexpr int CPB = (kThreads / 32) * CPW;   // cells per block
-  constexpr int VB = R > kRbFast ? 2 : 4;      // velocities per lane per pass
+  constexpr int VB = R > 4 ? 2 : 4;            // velocities per lane per pass
   // float2 scratch per cell (even, so every cell's float4 blocks stay
   // 16-byte aligned)
   constexpr int CS = 2 * P * Q + 2 * Q * R + 2 * P + 4 * P * R;

@@ -109,7 +109,7 @@ kstap_status enqueue_detect(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, cons
                             int sm_count, int waves, cudaStream_t s) {
   if (JL.njobs < 1) return KSTAP_OK;
   if (g.r_a == 2) return enqueue_detect_fp32<P, Q, R, 2>(ctx, prof, g, JL, sm_count, waves, s);
-  if constexpr (P <= 3 && R <= kstap::kRbFast) {
+  if constexpr (P <= 3 && R <= kstap::kRbTc) {
     if (ctx->prm.precision == KSTAP_FP16X3)
       return enqueue_detect_tc<P, Q, R, false>(ctx, prof, g, JL, sm_count, waves, s);
     if (ctx->prm.precision == KSTAP_BF16X3)
@@ -142,7 +142,7 @@ template <int P, int Q, int R = 1>
 kstap_status fit_rb(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                     char* scratch, const Layout& L, bool lag_store, int sm_count, int waves,
                     cudaStream_t s) {
-  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : kstap::kRbFast)) {
+  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : 4)) {
     if (g.r_b == R)
       return enqueue_fit<P, Q, R>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);
     return fit_rb<P, Q, R + 1>(ctx, prof, g, JL, scratch, L, lag_store, sm_count, waves, s);
@@ -152,7 +152,7 @@ kstap_status fit_rb(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobLis
 template <int P, int Q, int R = 1>
 kstap_status detect_rb(kstap_ctx* ctx, kstap_ctx* prof, const Geom& g, const JobList& JL,
                        int sm_count, int waves, cudaStream_t s) {
-  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : kstap::kRbFast)) {
+  if constexpr (R < Q && R <= (P <= 3 ? kstap::kRbMax : 4)) {
     if (g.r_b == R) return enqueue_detect<P, Q, R>(ctx, prof, g, JL, sm_count, waves, s);
     return detect_rb<P, Q, R + 1>(ctx, prof, g, JL, sm_count, waves, s);
   }

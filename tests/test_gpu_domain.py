@@ -4,8 +4,8 @@ Beyond the configurations' q in {8, 16, 32} and r_b in {2, 3, 4}, the
 library takes q in {12, 24} (a cell's q rows on a group of 16 or 32 lanes,
 the lanes past q idle; the tensor-core bank pads its contraction to whole
 K steps of 16) and any 1 <= r_b <= min(q - 1, 8) (Sec. 4's EIG_{r_b}; ranks
-above 4 take the block Rayleigh-Ritz path for every cell, on the
-single-precision bank).  Every case is checked element by element: T of
+above 4 on the single-precision bank).  Every case is checked element by
+element: T of
 every cell and velocity within the route's bar, maps outside the band
 around tau, argmax where resolvable, projectors and eigenvalues.
 """
@@ -68,16 +68,17 @@ def test_tensor_core_bank_q12_q24(precision, name, H, W, r_b):
 
 
 @pytest.mark.parametrize("name,r_b", [
-    ("small64", 5),       # q = 8: the block is the whole space (K = q)
+    ("small64", 5),       # q = 8
     ("frame_q12", 6),
-    ("frame1024", 8),     # q = 16, K = 12
+    ("frame1024", 8),     # q = 16
     ("frame_q24", 7),
     ("precision2048", 5),
     ("precision2048", 8),
 ])
 def test_parity_high_rank_b(name, r_b):
-    """r_b > 4: every cell's U_B from block subspace iteration with
-    K = min(q, r_b + 4) vectors and an FP64 Rayleigh-Ritz step."""
+    """r_b > 4: the subspace iteration on r_b vectors (its r_b x r_b Gram,
+    Cholesky and Ritz matrices spill from registers), with the block
+    Rayleigh-Ritz path on min(q, r_b + 4) vectors for ill-gapped cells."""
     wl = _wl(name, 9, 37, r_b=r_b)
     f = gen.make_frame(wl)
     ref = oracle.run_workload(f)
