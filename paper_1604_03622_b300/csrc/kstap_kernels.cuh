@@ -1080,19 +1080,27 @@ __device__ __forceinline__ ff grp_sum_ff(ff v) {
   return v;
 }
 
-// Modified Gram-Schmidt over the lanes of a group (FP32).
-template <int Q, int R>
-__device__ __forceinline__ void orthonormalise_g(float2 (&x)[R]) {
-  constexpr int G = grp_lanes(Q);
+// Modified Gram-Schmidt of R columns over a group of G lanes holding RP
+// rows each (FP32; rows that do not exist are zeros).
+template <int G, int RP, int R>
+__device__ __forceinline__ void orthonormalise_g(float2 (&x)[RP][R]) {
 #pragma unroll
   for (int m = 0; m < R; ++m) {
 #pragma unroll
     for (int mp = 0; mp < m; ++mp) {
-      const float2 cc = grp_sum2<G>(cmulc(x[mp], x[m]));
-      x[m] = csub(x[m], cmul(x[mp], cc));
+      float2 d = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < RP; ++k) d = cadd(d, cmulc(x[k][mp], x[k][m]));
+      const float2 cc = grp_sum2<G>(d);
+#pragma unroll
+      for (int k = 0; k < RP; ++k) x[k][m] = csub(x[k][m], cmul(x[k][mp], cc));
     }
-    const float nrm = sqrtf(grp_sum<G>(cabs2(x[m])));
-    x[m] = cscale(x[m], nrm > 0.f ? 1.f / nrm : 0.f);
+    float n2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < RP; ++k) n2 += cabs2(x[k][m]);
+    const float nrm = sqrtf(grp_sum<G>(n2));
+#pragma unroll
+    for (int k = 0; k < RP; ++k) x[k][m] = cscale(x[k][m], nrm > 0.f ? 1.f / nrm : 0.f);
   }
 }
 
@@ -1154,11 +1162,22 @@ __device__ __forceinline__ void ritz_values(const float2 (&H)[R][R], float (&lam
   }
 }
 
+// Rows of one cell per lane in the eigen phase of the B pass: two for
+// 12 <= q <= 24, so that a cell takes a group of eig_lanes(q) lanes (8 at
+// q = 12 and 16, 16 at q = 24) and the r_b x r_b work that every lane of a
+// group repeats (Cholesky factor, Ritz values, convergence bound) serves twice
+// as many cells per warp; lane jl of a group holds rows jl + k q / 2, k < 2.
+// At q = 32 a 16-cell tile already fills the 16 warps of its CTA with one row
+// per lane (two rows per lane left half of them idle: B pass 128 -> 179 ms
+// on the 2048^2 frame).
+__host__ __device__ constexpr int eig_rpl(int q) { return (q >= 12 && q <= 24) ? 2 : 1; }
+__host__ __device__ constexpr int eig_lanes(int q) { return grp_lanes(q / eig_rpl(q)); }
+
 constexpr float kSubTol = 1e-8f;   // accepted error of the leading subspace of B
 constexpr int kSubSteps = 4;       // float-float subspace steps before a cell is handed on
 
-// Leading R-dimensional eigenspace of one cell's B (group of Q lanes, lane j
-// = row j).  Start: R columns of B (they lie mostly in the clutter subspace),
+// Leading R-dimensional eigenspace of one cell's B (a group of eig_lanes(Q)
+// lanes, eig_rpl(Q) rows per lane).  Start: R columns of B (they lie mostly in the clutter subspace),
 // orthonormalised; one FP32 subspace step on B_hi; then float-float subspace
 // steps Y = B V with Cholesky-QR, U = Y L^-H.  Each step measures how far it
 // moved the subspace, c_k = |U - V V^H U|_F = |(Y - V H) L^-H|_F with
@@ -1176,90 +1195,120 @@ constexpr int kSubSteps = 4;       // float-float subspace steps before a cell i
 // on zeros).
 template <int Q, int R>
 __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int jl, bool live,
-                                 float2* __restrict__ Vs, float2 (&uh)[R], float2 (&ul)[R],
-                                 float (&lam)[R]) {
-  constexpr int G = grp_lanes(Q);
-  // lane jl of the group holds row j = jl; lanes jl >= Q (q not a power of
+                                 float2* __restrict__ Vs, float2 (&uh)[eig_rpl(Q)][R],
+                                 float2 (&ul)[eig_rpl(Q)][R], float (&lam)[R]) {
+  constexpr int RP = eig_rpl(Q), QL = Q / RP, G = eig_lanes(Q);
+  // rows j[k] = jl + k QL of lane jl; lanes jl >= QL (q / RP not a power of
   // two) hold zeros and compute on row 0 without keeping the result
-  const bool row = jl < Q;
-  const int j = row ? jl : 0;
-  float2 v[R], y[R];
+  bool row[RP];
+  int j[RP];
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
-    const float4 b = b_at<Q>(Bc, j, ((2 * m + 1) * Q) / (2 * R));
-    v[m] = row ? make_float2(b.x, b.y) : make_float2(0.f, 0.f);
+  for (int k = 0; k < RP; ++k) {
+    row[k] = jl < QL;
+    j[k] = row[k] ? jl + k * QL : 0;
   }
-  orthonormalise_g<Q, R>(v);
-  if (row) {
+  float2 v[RP][R], y[RP][R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
-  }
+  for (int k = 0; k < RP; ++k)
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const float4 b = b_at<Q>(Bc, j[k], ((2 * m + 1) * Q) / (2 * R));
+      v[k][m] = row[k] ? make_float2(b.x, b.y) : make_float2(0.f, 0.f);
+    }
+  orthonormalise_g<G, RP, R>(v);
+#pragma unroll
+  for (int k = 0; k < RP; ++k)
+    if (row[k]) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) Vs[m * Q + j[k]] = v[k][m];
+    }
   __syncwarp();
-  b_times_v_fp32<Q, R>(Bc, j, Vs, y);
-  if (!row) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) y[m] = make_float2(0.f, 0.f);
+  for (int k = 0; k < RP; ++k) {
+    b_times_v_fp32<Q, R>(Bc, j[k], Vs, y[k]);
+    if (!row[k]) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) y[k][m] = make_float2(0.f, 0.f);
+    }
   }
   __syncwarp();
   // Gram-Schmidt keeps orthonormality to ~eps cond(B V), which the change
   // measure of the float-float step below relies on (a one-pass Cholesky-QR
   // of the unnormalised start would leave ~eps cond^2)
-  orthonormalise_g<Q, R>(y);
+  orthonormalise_g<G, RP, R>(y);
   // tr B (for the bound on lambda_{R+1})
-  const float trB = grp_sum<G>(row ? b_at<Q>(Bc, j, j).x : 0.f);
+  float trl = 0.f;
 #pragma unroll
-  for (int m = 0; m < R; ++m) v[m] = y[m];
+  for (int k = 0; k < RP; ++k) trl += row[k] ? b_at<Q>(Bc, j[k], j[k]).x : 0.f;
+  const float trB = grp_sum<G>(trl);
+#pragma unroll
+  for (int k = 0; k < RP; ++k)
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[k][m] = y[k][m];
 
-  cff U[R];
+  cff U[RP][R];
   float2 H[R][R];
   bool converged = !live;
   for (int step = 0; step < kSubSteps; ++step) {
-    if (row) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) Vs[m * Q + j] = v[m];
-    }
+    for (int k = 0; k < RP; ++k)
+      if (row[k]) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) Vs[m * Q + j[k]] = v[k][m];
+      }
     __syncwarp();
-    // packed pairs: (re, im) += (br, bi) xr and (x, y) += (br, bi) (xi, -xi),
-    // then re = re1 + y, im = im1 + x (error-free merge)
-    float2 s1[R], c1[R], s2[R], c2[R];
+    cff Yf[RP][R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) s1[m] = c1[m] = s2[m] = c2[m] = make_float2(0.f, 0.f);
+    for (int k = 0; k < RP; ++k) {
+      // packed pairs: (re, im) += (br, bi) xr and (x, y) += (br, bi) (xi, -xi),
+      // then re = re1 + y, im = im1 + x (error-free merge)
+      float2 s1[R], c1[R], s2[R], c2[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) s1[m] = c1[m] = s2[m] = c2[m] = make_float2(0.f, 0.f);
+      const int jj = j[k];
 #pragma unroll 2
-    for (int t = 0; t < Q; ++t) {
-      const int l = (j + t < Q) ? j + t : j + t - Q;
-      const float4 b = b_at<Q>(Bc, j, l);
-      const float2 xh = make_float2(b.x, b.y), xl = make_float2(b.z, b.w);
-      const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
+      for (int t = 0; t < Q; ++t) {
+        const int l = (jj + t < Q) ? jj + t : jj + t - Q;
+        const float4 b = b_at<Q>(Bc, jj, l);
+        const float2 xh = make_float2(b.x, b.y), xl = make_float2(b.z, b.w);
+        const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const float2 x = Vs[m * Q + l];
+          acc_ffxf2(s1[m], c1[m], xh, nxh, xl, make_float2(x.x, x.x));
+          acc_ffxf2(s2[m], c2[m], xh, nxh, xl, make_float2(x.y, -x.y));
+        }
+      }
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        const float2 x = Vs[m * Q + l];
-        acc_ffxf2(s1[m], c1[m], xh, nxh, xl, make_float2(x.x, x.x));
-        acc_ffxf2(s2[m], c2[m], xh, nxh, xl, make_float2(x.y, -x.y));
+        float sr, er, si, ei;
+        two_sum(s1[m].x, s2[m].y, sr, er);
+        two_sum(s1[m].y, s2[m].x, si, ei);
+        Yf[k][m] = row[k] ? cff{ff_make(sr, __fadd_rn(er, __fadd_rn(c1[m].x, c2[m].y))),
+                                ff_make(si, __fadd_rn(ei, __fadd_rn(c1[m].y, c2[m].x)))}
+                          : cff_zero();
       }
     }
     __syncwarp();
-    cff Yf[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-      float sr, er, si, ei;
-      two_sum(s1[m].x, s2[m].y, sr, er);
-      two_sum(s1[m].y, s2[m].x, si, ei);
-      Yf[m] = row ? cff{ff_make(sr, __fadd_rn(er, __fadd_rn(c1[m].x, c2[m].y))),
-                        ff_make(si, __fadd_rn(ei, __fadd_rn(c1[m].y, c2[m].x)))}
-                  : cff_zero();
-    }
     // H = V^H Y (FP32), Gram G = Y^H Y (float-float)
 #pragma unroll
     for (int m = 0; m < R; ++m)
 #pragma unroll
-      for (int mp = 0; mp < R; ++mp)
-        H[m][mp] = grp_sum2<G>(cmulc(v[m], make_float2(Yf[mp].re.hi, Yf[mp].im.hi)));
+      for (int mp = 0; mp < R; ++mp) {
+        float2 d = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < RP; ++k)
+          d = cadd(d, cmulc(v[k][m], make_float2(Yf[k][mp].re.hi, Yf[k][mp].im.hi)));
+        H[m][mp] = grp_sum2<G>(d);
+      }
     cff Gm[R][R];
 #pragma unroll
     for (int m = 0; m < R; ++m)
 #pragma unroll
       for (int mp = m; mp < R; ++mp) {
-        const cff pr = cff_cmul(Yf[m], Yf[mp]);
+        cff pr = cff_cmul(Yf[0][m], Yf[0][mp]);
+#pragma unroll
+        for (int k = 1; k < RP; ++k) pr = cff_add(pr, cff_cmul(Yf[k][m], Yf[k][mp]));
         Gm[m][mp] = cff{grp_sum_ff<G>(pr.re), grp_sum_ff<G>(pr.im)};
       }
     // Cholesky G = L L^H
@@ -1280,27 +1329,31 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int jl, bool liv
         L[i][m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
       }
     }
-    // U = Y L^-H (row j)
+    // U = Y L^-H (rows j[k])
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      cff t = Yf[m];
+    for (int k = 0; k < RP; ++k)
 #pragma unroll
-      for (int k = 0; k < m; ++k) t = cff_sub(t, cff_mul(U[k], cff{L[m][k].re, ff_neg(L[m][k].im)}));
-      const ff lmm = L[m][m].re;
-      U[m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
-    }
-    // change of the subspace: (I - V V^H) U = (Y - V H) L^-H, row j (FP32;
-    // the residual is formed directly, so small changes do not cancel)
+      for (int m = 0; m < R; ++m) {
+        cff t = Yf[k][m];
+#pragma unroll
+        for (int i = 0; i < m; ++i)
+          t = cff_sub(t, cff_mul(U[k][i], cff{L[m][i].re, ff_neg(L[m][i].im)}));
+        const ff lmm = L[m][m].re;
+        U[k][m] = (lmm.hi > 0.f) ? cff{ff_div(t.re, lmm), ff_div(t.im, lmm)} : cff_zero();
+      }
+    // change of the subspace: (I - V V^H) U = (Y - V H) L^-H, rows j[k]
+    // (FP32; the residual is formed directly, so small changes do not cancel)
     float local = 0.f;
-    {
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
       float2 X[R];
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        float2 t = make_float2(Yf[m].re.hi, Yf[m].im.hi);
+        float2 t = make_float2(Yf[k][m].re.hi, Yf[k][m].im.hi);
 #pragma unroll
-        for (int mp = 0; mp < R; ++mp) t = csub(t, cmul(v[mp], H[mp][m]));
+        for (int mp = 0; mp < R; ++mp) t = csub(t, cmul(v[k][mp], H[mp][m]));
 #pragma unroll
-        for (int k = 0; k < m; ++k) t = csub(t, cmul(X[k], make_float2(L[m][k].re.hi, -L[m][k].im.hi)));
+        for (int i = 0; i < m; ++i) t = csub(t, cmul(X[i], make_float2(L[m][i].re.hi, -L[m][i].im.hi)));
         const float lmm = L[m][m].re.hi;
         X[m] = (lmm > 0.f) ? cscale(t, 1.f / lmm) : make_float2(0.f, 0.f);
         local += cabs2(X[m]);
@@ -1308,7 +1361,9 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int jl, bool liv
     }
     const float change = grp_sum<G>(local);
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = make_float2(U[m].re.hi, U[m].im.hi);
+    for (int k = 0; k < RP; ++k)
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[k][m] = make_float2(U[k][m].re.hi, U[k][m].im.hi);
     ritz_values<R>(H, lam);
     float rs = 0.f;
 #pragma unroll
@@ -1320,10 +1375,12 @@ __device__ bool eig_top_subspace(const float4* __restrict__ Bc, int jl, bool liv
     if (__all_sync(0xffffffffu, converged)) break;
   }
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
-    uh[m] = make_float2(U[m].re.hi, U[m].im.hi);
-    ul[m] = make_float2(U[m].re.lo, U[m].im.lo);
-  }
+  for (int k = 0; k < RP; ++k)
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      uh[k][m] = make_float2(U[k][m].re.hi, U[k][m].im.hi);
+      ul[k][m] = make_float2(U[k][m].re.lo, U[k][m].im.lo);
+    }
   return converged;
 }
 
@@ -1685,7 +1742,7 @@ __host__ __device__ constexpr int bfit_lag_bytes(int P, int Q, int TC, int Ra, b
          (from_store ? 0 : 2 * P * P * (TC + 2 * Ra + Q - 1) * 16);
 }
 __host__ __device__ constexpr int bfit_basis_bytes(int Q, int R) {
-  return (bfit_threads(Q) / 32) * (32 / grp_lanes(Q)) * Q * R * 8;
+  return (bfit_threads(Q) / 32) * (32 / eig_lanes(Q)) * Q * R * 8;
 }
 __host__ __device__ constexpr int imax3(int a, int b, int c) {
   return a > b ? (a > c ? a : c) : (b > c ? b : c);
@@ -1752,7 +1809,8 @@ __global__ void __launch_bounds__(bfit_threads(Q), 65536 / 128 / bfit_threads(Q)
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
-  constexpr int GL = grp_lanes(Q);   // lanes per cell in the eigen phase
+  constexpr int GL = eig_lanes(Q);   // lanes per cell in the eigen phase
+  constexpr int RP = eig_rpl(Q);     // rows per lane in the eigen phase
   constexpr int CPW = 32 / GL;       // cells per warp in the eigen phase
   constexpr int NT = bfit_threads(Q);
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1913,11 +1971,14 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
     const int cl = base + slot;
     const bool live = cl < TC && (c0 + cl) < g.W;
     const int clc = live ? cl : 0;
-    float2 uh[R], ul[R];
+    float2 uh[RP][R], ul[RP][R];
     float lam[R];
     const bool conv =
         eig_top_subspace<Q, R>(Bs + clc * NB, j, live, Vs + slot * Q * R, uh, ul, lam);
-    if (live && conv && j < Q) store(cl, j, uh, ul, lam);
+    if (live && conv && j < Q / RP) {
+#pragma unroll
+      for (int k = 0; k < RP; ++k) store(cl, j + k * (Q / RP), uh[k], ul[k], lam);
+    }
     if (live && !conv && j == 0) fb_cell[atomicAdd(&fb_n, 1)] = cl;
   }
   __syncthreads();
