@@ -74,7 +74,10 @@ def test_stacked_pass_parity(name, H, W, r_a, r_b):
     assert np.abs(PB - ref["PB"]).max() < 1e-7
     np.testing.assert_allclose(gpu["lamA"], ref["lamA"], rtol=1e-4)
     np.testing.assert_allclose(gpu["lamB"], ref["lamB"], rtol=1e-4)
-    np.testing.assert_allclose(gpu["eta"], ref["eta"], rtol=2e-2, atol=2e-4)
+    # eta of Alg. 2 from the closed form eta^2 = 1 - a^H M a / (|a|^2 tr M) with M
+    # accumulated in single precision: the relative error of the ratio
+    # (~1e-6) over eta^2 (>= 2.5e-3 here) bounds eta's relative error by ~2e-4
+    np.testing.assert_allclose(gpu["eta"], ref["eta"], rtol=2e-4, atol=1e-6)
     print(name, H, W, r_a, r_b, rep)
 
 

@@ -45,8 +45,10 @@ def test_parity_full_small_frames(name, H, W):
     # eigenvalues of the trace-normalised factors
     np.testing.assert_allclose(gpu["lamA"], ref["lamA"], rtol=1e-5)
     np.testing.assert_allclose(gpu["lamB"], ref["lamB"], rtol=1e-4)
-    # eta (closed form in FP64 from the single-precision M)
-    np.testing.assert_allclose(gpu["eta"], ref["eta"], rtol=2e-2, atol=2e-4)
+    # eta of Alg. 2 from the closed form eta^2 = 1 - a^H M a / (|a|^2 tr M) with M
+    # accumulated in single precision: the relative error of the ratio
+    # (~1e-6) over eta^2 (>= 2.5e-3 here) bounds eta's relative error by ~2e-4
+    np.testing.assert_allclose(gpu["eta"], ref["eta"], rtol=2e-4, atol=1e-6)
     print(name, H, W, rep)
 
 
