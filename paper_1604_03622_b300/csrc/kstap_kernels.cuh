@@ -2005,6 +2005,77 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
   }  // tile loop
 }
 
+
+// ------------------------------------------------ projection helpers -------
+// Splits of the j sum of a per-cell contraction over a group of G lanes with
+// NI outputs: the largest power of two S with S NI <= G that divides q (so
+// that S NI lanes work where NI would, the rest of the group idle).
+__host__ __device__ constexpr int split_j(int q, int g, int ni) {
+  int s = 1;
+  while (2 * s * ni <= g && q % (2 * s) == 0) s *= 2;
+  return s;
+}
+
+// C[i][m] = sum_j X[i][j] conj(U[j][m]) of one cell, float-float (U = hi +
+// lo), into Cs[i R + m] as (re_hi, re_lo, im_hi, im_lo).  With S =
+// split_j(Q, G, P R) > 1, lane gl of the group takes output gl % (P R) over
+// the j range of split gl / (P R), and the S compensated partial sums are
+// merged by shuffles.  Every lane of the warp calls it (the merge shuffles
+// over the whole warp); live = this group's cell exists.
+template <int P, int Q, int R, int G>
+__device__ __forceinline__ void xconj_u_ff(const float2* __restrict__ Xs,
+                                           const float2* __restrict__ Uh,
+                                           const float2* __restrict__ Ul, float4* __restrict__ Cs,
+                                           int gl, bool live) {
+  constexpr int NI = P * R, S = split_j(Q, G, NI), QS = Q / S;
+  auto partial = [&](int it, int j0, int j1, float& sr, float& cr, float& si, float& ci) {
+    const int i = it / R, m = it % R;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+      const float2 x = Xs[i * Q + j];
+      const float2 uh = Uh[j * R + m], ul = Ul[j * R + m];
+      acc_ffxf(sr, cr, uh.x, ul.x, x.x);    // re += ur xr + ui xi
+      acc_ffxf(sr, cr, uh.y, ul.y, x.y);
+      acc_ffxf(si, ci, uh.x, ul.x, x.y);    // im += ur xi - ui xr
+      acc_ffxf(si, ci, uh.y, ul.y, -x.x);
+    }
+  };
+  if constexpr (S == 1) {
+    if (live) {
+      for (int it = gl; it < NI; it += G) {
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        partial(it, 0, Q, sr, cr, si, ci);
+        const ff re = ff_make(sr, cr), im = ff_make(si, ci);
+        Cs[it] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+    }
+  } else {
+    const int sp = gl / NI, it = gl - sp * NI;
+    const bool act = live && sp < S;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    if (act) partial(it, sp * QS, sp * QS + QS, sr, cr, si, ci);
+    // split sp receives split sp + h (lane + h NI, inside the group)
+#pragma unroll
+    for (int h = S / 2; h >= 1; h >>= 1) {
+      const float a = __shfl_down_sync(0xffffffffu, sr, h * NI);
+      const float b = __shfl_down_sync(0xffffffffu, cr, h * NI);
+      const float c = __shfl_down_sync(0xffffffffu, si, h * NI);
+      const float d = __shfl_down_sync(0xffffffffu, ci, h * NI);
+      float t, e;
+      two_sum(sr, a, t, e);
+      sr = t;
+      cr = __fadd_rn(cr, __fadd_rn(b, e));
+      two_sum(si, c, t, e);
+      si = t;
+      ci = __fadd_rn(ci, __fadd_rn(d, e));
+    }
+    if (act && sp == 0) {
+      const ff re = ff_make(sr, cr), im = ff_make(si, ci);
+      Cs[it] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+  }
+}
+
 // ------------------------------------------------ K4: detect ---------------
 // A group of Q lanes per cell (32/Q cells per warp).  Per cell:
 //   C  = X conj(U_B)                 (P x R, float-float; one lane per (i, m))
@@ -2114,23 +2185,7 @@ k_detect(Geom g0, JobList JL, const float2* __restrict__ bank_aT,
   __syncwarp();
   prefetch(tile + gridDim.x);
   // C[i][m] = sum_j X[i][j] conj(U[j][m]), float-float
-  if (live) {
-    for (int it = gl; it < P * R; it += G) {
-      const int i = it / R, m = it % R;
-      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < Q; ++j) {
-        const float2 x = Xs[i * Q + j];
-        const float2 uh = Uh[j * R + m], ul = Ul[j * R + m];
-        acc_ffxf(sr, cr, uh.x, ul.x, x.x);    // re += ur xr + ui xi
-        acc_ffxf(sr, cr, uh.y, ul.y, x.y);
-        acc_ffxf(si, ci, uh.x, ul.x, x.y);    // im += ur xi - ui xr
-        acc_ffxf(si, ci, uh.y, ul.y, -x.x);
-      }
-      const ff re = ff_make(sr, cr), im = ff_make(si, ci);
-      Cs[i * R + m] = make_float4(re.hi, re.lo, im.hi, im.lo);
-    }
-  }
+  xconj_u_ff<P, Q, R, G>(Xs, Uh, Ul, Cs, gl, live);
   __syncwarp();
   const bool classical = g.filter == 1;
   if (classical && live) {

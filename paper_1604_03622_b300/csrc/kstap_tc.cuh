@@ -255,23 +255,7 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
       }
       __syncwarp();
       // C = X conj(U_B), float-float
-      if (live) {
-        for (int it = gl; it < P * R; it += G) {
-          const int i = it / R, m = it % R;
-          float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-#pragma unroll 4
-          for (int j = 0; j < Q; ++j) {
-            const float2 x = Xs[i * Q + j];
-            const float2 uh = Uh[j * R + m], ul = Ul[j * R + m];
-            acc_ffxf(sr, cr, uh.x, ul.x, x.x);
-            acc_ffxf(sr, cr, uh.y, ul.y, x.y);
-            acc_ffxf(si, ci, uh.x, ul.x, x.y);
-            acc_ffxf(si, ci, uh.y, ul.y, -x.x);
-          }
-          const ff re = ff_make(sr, cr), im = ff_make(si, ci);
-          Cs[i * R + m] = make_float4(re.hi, re.lo, im.hi, im.lo);
-        }
-      }
+      xconj_u_ff<P, Q, R, G>(Xs, Uh, Ul, Cs, gl, live);
       __syncwarp();
       float2 z[P];
       float zmax = 0.f;
@@ -310,14 +294,36 @@ k_detect_tc(Geom g0, JobList JL, const uint4* __restrict__ bank_op, float bank_i
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
       __syncwarp();
-      // E = Z conj(U_hi): the part of Z left in span(conj U_B) by rounding
-      if (live) {
-        for (int it = gl; it < P * R; it += G) {
+      // E = Z conj(U_hi): the part of Z left in span(conj U_B) by rounding;
+      // the j sum split over the group's otherwise idle lanes as for C
+      {
+        constexpr int NI = P * R, S = split_j(Q, G, NI), QS = Q / S;
+        const int sp = gl / NI, it = gl - sp * NI;
+        const bool act = live && sp < S;
+        float2 e = make_float2(0.f, 0.f);
+        if (act) {
           const int i = it / R, m = it % R;
-          float2 s = make_float2(0.f, 0.f);
 #pragma unroll 4
-          for (int j = 0; j < Q; ++j) s = cadd(s, cmul(Zs[i * Q + j], cconj(Uh[j * R + m])));
-          Es[i * R + m] = s;
+          for (int j = sp * QS; j < sp * QS + QS; ++j)
+            e = cadd(e, cmul(Zs[i * Q + j], cconj(Uh[j * R + m])));
+        }
+#pragma unroll
+        for (int h = S / 2; h >= 1; h >>= 1) {
+          e.x += __shfl_down_sync(0xffffffffu, e.x, h * NI);
+          e.y += __shfl_down_sync(0xffffffffu, e.y, h * NI);
+        }
+        if (act && sp == 0) Es[it] = e;
+        if constexpr (S == 1) {
+          // more outputs than lanes: the rest, one lane each
+          if (live) {
+            for (int it2 = gl + G; it2 < NI; it2 += G) {
+              const int i = it2 / R, m = it2 % R;
+              float2 e2 = make_float2(0.f, 0.f);
+#pragma unroll 4
+              for (int j = 0; j < Q; ++j) e2 = cadd(e2, cmul(Zs[i * Q + j], cconj(Uh[j * R + m])));
+              Es[it2] = e2;
+            }
+          }
         }
       }
       // power-of-two scale putting max |Z| in [0.5, 1): FP16 range and
