@@ -1788,6 +1788,13 @@ struct BAcc {
     acc_ffxf2(s1, c1, xh, nxh, xl, make_float2(ya.x, ya.y));
     acc_ffxf2(s2, c2, xh, nxh, xl, make_float2(ya.z, ya.w));
   }
+  // a term with a real a_J (the diagonal J = i + P i of the Hermitian a,
+  // stored with a zero imaginary part): only the (re, im) += L ar chain
+  __device__ __forceinline__ void add_real(float4 ya, float4 L) {
+    const float2 xh = make_float2(L.x, L.y), xl = make_float2(L.z, L.w);
+    const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
+    acc_ffxf2(s1, c1, xh, nxh, xl, make_float2(ya.x, ya.y));
+  }
   // (re_hi, im_hi, re_lo, im_lo), the layout of the tile's B entries
   __device__ __forceinline__ float4 get() const {
     float s, e;
@@ -1881,7 +1888,14 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
     const int cl = e / nj, j = e - cl * nj;
     BAcc b;
 #pragma unroll
-    for (int J = 0; J < PP; ++J) b.add(as[cl * PP + J], lb[J * NUmax + cl + j]);
+    for (int J = 0; J < PP; ++J) {
+      // the flip-flop stores a exactly Hermitian with a real diagonal, so the
+      // diagonal terms' imaginary chain would add exact zeros
+      if (J % (P + 1) == 0)
+        b.add_real(as[cl * PP + J], lb[J * NUmax + cl + j]);
+      else
+        b.add(as[cl * PP + J], lb[J * NUmax + cl + j]);
+    }
     Bs[cl * NB + diag_off<Q>(lagg) + j] = b.get();
   };
   if (FROM_STORE) {
