@@ -303,6 +303,35 @@ __device__ __forceinline__ void ll_to_ff(long long v, float& hi, float& lo) {
   quick_two_sum(s, __fadd_rn(e, f0), hi, lo);
 }
 
+// Plane groups of the single-pass lag planes (p <= 3): group gi < P is the
+// diagonal plane J = i + P i alone (j2 = -1); the others are the pairs
+// (j1 = i + P k, j2 = k + P i), i < k.  The B pass replaces a pair's planes
+// in its tile buffers by S = L_j1 + L_j2 at j1 and D = L_j1 - L_j2 at j2,
+// because with a Hermitian a (a_j2 = conj(a_j1)) the pair's part of
+// B = sum_J conj(a_J) L_J is Re(a_j1) S - i Im(a_j1) D: two real-coefficient
+// float-float products per entry instead of two complex ones.
+template <int P>
+__device__ __forceinline__ void plane_group(int gi, int& j1, int& j2) {
+  if (gi < P) {
+    j1 = gi * (P + 1);
+    j2 = -1;
+    return;
+  }
+  int idx = gi - P;
+  j1 = 0;
+  j2 = -1;
+#pragma unroll
+  for (int i = 0; i < P; ++i)
+#pragma unroll
+    for (int k = i + 1; k < P; ++k) {
+      if (idx == 0) {
+        j1 = i + P * k;
+        j2 = k + P * i;
+      }
+      --idx;
+    }
+}
+
 constexpr int kMomRows = 4;                         // cell rows per CTA in the moments pass
 constexpr int kMomThreads = kTileCells * kMomRows;  // one thread per cell
 constexpr int kHChunk = 3;                          // positions per item in the running ring sums
@@ -1788,12 +1817,20 @@ struct BAcc {
     acc_ffxf2(s1, c1, xh, nxh, xl, make_float2(ya.x, ya.y));
     acc_ffxf2(s2, c2, xh, nxh, xl, make_float2(ya.z, ya.w));
   }
-  // a term with a real a_J (the diagonal J = i + P i of the Hermitian a,
-  // stored with a zero imaginary part): only the (re, im) += L ar chain
+  // a term with a real coefficient ar: only the (re, im) += L ar chain (the
+  // diagonal J = i + P i of the Hermitian a, stored with a zero imaginary
+  // part, and a pair's S plane)
   __device__ __forceinline__ void add_real(float4 ya, float4 L) {
     const float2 xh = make_float2(L.x, L.y), xl = make_float2(L.z, L.w);
     const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
     acc_ffxf2(s1, c1, xh, nxh, xl, make_float2(ya.x, ya.y));
+  }
+  // -i ai L (a pair's D plane, ya of the pair's upper a): only the second
+  // chain, (x, y) += (Lr, Li) (-ai, ai)
+  __device__ __forceinline__ void add_imag(float4 ya, float4 L) {
+    const float2 xh = make_float2(L.x, L.y), xl = make_float2(L.z, L.w);
+    const float2 nxh = f2_mul(xh, make_float2(-1.f, -1.f));
+    acc_ffxf2(s2, c2, xh, nxh, xl, make_float2(ya.z, ya.w));
   }
   // (re_hi, im_hi, re_lo, im_lo), the layout of the tile's B entries
   __device__ __forceinline__ float4 get() const {
@@ -1816,6 +1853,7 @@ __global__ void __launch_bounds__(bfit_threads(Q), 65536 / 128 / bfit_threads(Q)
 k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restrict__ Lw0) {
   constexpr int PP = P * P;
   constexpr int NB = Q * (Q + 1) / 2;
+  constexpr bool kPairs = P <= 3;    // the single-pass lag planes hold pair sums / differences
   constexpr int GL = eig_lanes(Q);   // lanes per cell in the eigen phase
   constexpr int RP = eig_rpl(Q);     // rows per lane in the eigen phase
   constexpr int CPW = 32 / GL;       // cells per warp in the eigen phase
@@ -1890,9 +1928,15 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
 #pragma unroll
     for (int J = 0; J < PP; ++J) {
       // the flip-flop stores a exactly Hermitian with a real diagonal, so the
-      // diagonal terms' imaginary chain would add exact zeros
-      if (J % (P + 1) == 0)
+      // diagonal terms' imaginary chain would add exact zeros.  Single pass:
+      // the off-diagonal planes hold a pair's S (at i + P k, i < k) and D (at
+      // k + P i), taken with Re(a_{i + P k}) and -i Im(a_{i + P k})
+      // (plane_group); stacked passes: every plane is L_J itself
+      const int i = J % P, k = J / P;
+      if (J % (P + 1) == 0 || (kPairs && i < k))
         b.add_real(as[cl * PP + J], lb[J * NUmax + cl + j]);
+      else if (kPairs)
+        b.add_imag(as[cl * PP + k + P * i], lb[J * NUmax + cl + j]);
       else
         b.add(as[cl * PP + J], lb[J * NUmax + cl + j]);
     }
@@ -1920,8 +1964,30 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
       const int la = lag_at(p0), lb_ = lag_at(p1 - 1);
       const int na = TC * (Q - la);
       const int tot = (p1 - p0 == 2) ? na + TC * (Q - lb_) : na;
-      const float4* bufa = lag + (p0 % kLagStages) * PP * NUmax;
-      const float4* bufb = lag + ((p1 - 1) % kLagStages) * PP * NUmax;
+      float4* bufa = lag + (p0 % kLagStages) * PP * NUmax;
+      float4* bufb = lag + ((p1 - 1) % kLagStages) * PP * NUmax;
+      if constexpr (kPairs) {
+        // each pair's planes -> S, D (float-float sums of the stored sums;
+        // their rounding, 2^-48 of the terms, is that of the stored sums)
+        constexpr int NPR = P * (P - 1) / 2;
+        const int nua = TC + Q - 1 - la, nub = TC + Q - 1 - lb_;
+        const int nitem = NPR * (nua + ((p1 - p0 == 2) ? nub : 0));
+        for (int idx = threadIdx.x; idx < nitem; idx += NT) {
+          const bool first = idx < NPR * nua;
+          const int r2 = first ? idx : idx - NPR * nua;
+          const int nu = first ? nua : nub;
+          const int pr = r2 / nu, u = r2 - pr * nu;
+          int J1, J2;
+          plane_group<P>(P + pr, J1, J2);
+          float4* bf = first ? bufa : bufb;
+          const float4 x = bf[J1 * NUmax + u], y = bf[J2 * NUmax + u];
+          const ff sr = ff_add(ff{x.x, x.z}, ff{y.x, y.z}), si = ff_add(ff{x.y, x.w}, ff{y.y, y.w});
+          const ff dr = ff_sub(ff{x.x, x.z}, ff{y.x, y.z}), di = ff_sub(ff{x.y, x.w}, ff{y.y, y.w});
+          bf[J1 * NUmax + u] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+          bf[J2 * NUmax + u] = make_float4(dr.hi, di.hi, dr.lo, di.lo);
+        }
+        __syncthreads();
+      }
       for (int idx = threadIdx.x; idx < tot; idx += NT) {
         const bool first = idx < na;
         b_entry(first ? la : lb_, first ? bufa : bufb, first ? idx : idx - na);
@@ -1939,9 +2005,25 @@ k_bfit(Geom g0, JobList JL, const float2* __restrict__ aw, const float4* __restr
       for (int idx = threadIdx.x; idx < PP * NU; idx += NT) {
         const int u = idx % NU, J = idx / NU;
         const longlong2 L = ring_sum(Vo + J * KW, Vg + J * KW, g, u);
+        const int i = J % P, k = J / P;
         float4 v;
         ll_to_ff(L.x, v.x, v.z);
         ll_to_ff(L.y, v.y, v.w);
+        if (kPairs && i != k) {
+          // the pair's S (at i + P k, i < k) or D (at k + P i), formed from
+          // the two planes' float-float values exactly as the lag-store
+          // branch forms them from the stored planes (plane_group), so the
+          // two branches stay bit-identical
+          const int Jm = k + P * i;
+          const longlong2 Lm = ring_sum(Vo + Jm * KW, Vg + Jm * KW, g, u);
+          float4 w;
+          ll_to_ff(Lm.x, w.x, w.z);
+          ll_to_ff(Lm.y, w.y, w.w);
+          const float4 x = (i < k) ? v : w, y = (i < k) ? w : v;   // planes j1, j2
+          const ff re = (i < k) ? ff_add(ff{x.x, x.z}, ff{y.x, y.z}) : ff_sub(ff{x.x, x.z}, ff{y.x, y.z});
+          const ff im = (i < k) ? ff_add(ff{x.y, x.w}, ff{y.y, y.w}) : ff_sub(ff{x.y, x.w}, ff{y.y, y.w});
+          v = make_float4(re.hi, im.hi, re.lo, im.lo);
+        }
         lag[J * NUmax + u] = v;
       }
       __syncthreads();
