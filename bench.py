@@ -295,17 +295,17 @@ def kernel_src_sha256() -> str:
 
 
 TRAFFIC = {
-    # 512 x 1024-cell capture (1.266 GB read + 0.398 GB write) x 2 for the 1024^2
+    # 512 x 1024-cell capture (1.265 GB read + 0.400 GB write) x 2 for the 1024^2
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.265806e9 + 0.398262e9),
+        bytes=2 * (1.264914e9 + 0.399594e9),
         # issue slots used (smsp__issue_active) and FMA-pipe activity of the
         # same capture: the kernel's float-float arithmetic costs ~10
         # instructions per algorithmic flop (packed f32x2 pairs issue two
         # lanes at once but hold the FMA pipe for two cycles)
-        issue_active=0.602, fma_pipe_active=0.555,
-        sha256="64164052b383148ff08a1fc560bf36d43544ad7bfc04e81c21861be3d1b76232",
+        issue_active=0.592, fma_pipe_active=0.494,
+        sha256="32e5dc5619861b04ef509804d53d9da2bf75981946f4ed3531902e00d6f40d5b",
         source="profiles/bfit_frame1024_512x1024.md"),
 }
 
