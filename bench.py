@@ -295,16 +295,16 @@ def kernel_src_sha256() -> str:
 
 
 TRAFFIC = {
-    # 512 x 1024-cell capture (1.265 GB read + 0.400 GB write) x 2 for the 1024^2
+    # 512 x 1024-cell capture (1.262 GB read + 0.389 GB write) x 2 for the 1024^2
     # frame: bfit's traffic is the lag store read once per position plus the
     # per-cell a and U_B hi/lo, so it grows with the cell count
     ("frame1024", "fp32", "bfit"): dict(
-        bytes=2 * (1.264914e9 + 0.399594e9),
+        bytes=2 * (1.262305e9 + 0.389270e9),
         # issue slots used (smsp__issue_active) and FMA-pipe activity of the
         # same capture: the kernel's float-float arithmetic costs ~10
         # instructions per algorithmic flop (packed f32x2 pairs issue two
         # lanes at once but hold the FMA pipe for two cycles)
-        issue_active=0.592, fma_pipe_active=0.494,
+        issue_active=0.607, fma_pipe_active=0.504,
         sha256="32e5dc5619861b04ef509804d53d9da2bf75981946f4ed3531902e00d6f40d5b",
         source="profiles/bfit_frame1024_512x1024.md"),
 }
@@ -830,7 +830,7 @@ def main():
     ks = KStap.from_workload(wl, frames[0].bank_a, frames[0].bank_b, device=str(dev),
                              precision=args.precision,
                              stream=stream)
-    K.kstap_set_tuning(ks.ctx, 4, 0, lag_store=args.lag_store)
+    K.kstap_set_tuning(ks.ctx, 64, 0, lag_store=args.lag_store)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ncell = wl.H * wl.W
 

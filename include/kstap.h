@@ -259,8 +259,10 @@ kstap_status kstap_graph_create(kstap_ctx* const* ctxs, const kstap_frame* const
 kstap_status kstap_graph_launch(kstap_graph* graph, void* cuda_stream);
 kstap_status kstap_graph_destroy(kstap_graph* graph);
 
-/* Launch tuning of a context.  waves: persistent grid size in multiples of
- * (SMs x resident CTAs), 1..64; tc: cells per tile of the B / U_B pass
+/* Launch tuning of a context.  waves: grid size in multiples of (SMs x
+ * resident CTAs), 1..64, capped by the tile count (default 64: one or two
+ * tiles per CTA on a megapixel frame; smaller values make each CTA stride
+ * over more tiles); tc: cells per tile of the B / U_B pass
  * (0 = default: 32, or 16 at q = 32; allowed 8, 16, 32 with tc = 32 only for
  * q <= 16); lag_store: 1 = the moments pass writes the exact lag sums to a
  * workspace store that the B pass reads (9 q (W + q - 1) x 16 B per cell row,
@@ -276,7 +278,7 @@ typedef struct {
 } kstap_tuning;
 
 /* Autotuner: times kstap_run_batch on these frames (reps repetitions after a
- * warm-up) for every candidate (waves in {1,2,4,8,16}) x (tc in {16,32}, or
+ * warm-up) for every candidate (waves in {1,2,4,8,16,32,64}) x (tc in {16,32}, or
  * {8,16} at q = 32) x (lag_store in {1, 0} for p = 3), keeps the fastest in
  * the context and reports it.  Synchronises the context stream. */
 kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, int reps,

@@ -835,7 +835,7 @@ kstap_status kstap_autotune(kstap_ctx* ctx, const kstap_frame* frames, int n, in
   ctx->profile = false;
   const std::vector<int> tcs =
       (ctx->prm.q >= 24) ? std::vector<int>{8, 16} : std::vector<int>{16, 32};
-  const int wavesv[] = {1, 2, 4, 8, 16};
+  const int wavesv[] = {1, 2, 4, 8, 16, 32, 64};
   std::vector<int> stores{1};
   if (ctx->prm.p <= 3) stores.push_back(0);
   cudaEvent_t a, b;

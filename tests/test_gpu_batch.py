@@ -37,7 +37,7 @@ def test_batch_bit_identical_to_per_frame_and_tuning_invariant():
     ref = []
     for Y in Ys:
         ref.append(_np(ks.run(Y, T_all=True)))
-    for waves, tc in ((4, 0), (1, 16), (16, 32)):
+    for waves, tc in ((4, 0), (1, 16), (16, 32), (64, 0)):
         K.kstap_set_tuning(ks.ctx, waves, tc)
         bufs = [ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
         K.kstap_run_batch(ks.ctx, [ks.frame_desc(Y, b) for Y, b in zip(Ys, bufs)])
@@ -96,7 +96,7 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     bufs = [ks.alloc_outputs(Y.shape[1], Y.shape[2], T_all=True) for Y in Ys]
     descs = [ks.frame_desc(Y, b) for Y, b in zip(Ys, bufs)]
     t = K.kstap_autotune(ks.ctx, descs, reps=2)
-    assert t.waves in (1, 2, 4, 8, 16) and t.tc in (16, 32) and t.ms_per_batch > 0
+    assert t.waves in (1, 2, 4, 8, 16, 32, 64) and t.tc in (16, 32) and t.ms_per_batch > 0
     K.kstap_run_batch(ks.ctx, descs)
     torch.cuda.synchronize()
     for r, b in zip(ref, bufs):
